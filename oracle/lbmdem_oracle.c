@@ -22,6 +22,12 @@
  *   5. K velocity-Verlet DEM substeps with Hertz normal and incremental
  *      Mindlin tangential contacts capped by Coulomb friction (Eqs. 9-12),
  *      the hydrodynamic force and torque held fixed over the K substeps.
+ *      The force and torque that drive the sphere in step t are the mean of
+ *      the sums of Eqs. 18-19 of steps t and t-1 (zero before the first
+ *      step): the half-way bounce-back force alternates from step to step
+ *      (Ladd's momentum-exchange method, cited in Section 2.3, averages it
+ *      over two steps), and applied raw it drives the fluid pockets at the
+ *      contact necks of spheres with rho_p / rho_f ~ 2.5 unstable.
  *
  * Readings where the paper is silent or garbled (each is stated where it is
  * used): index order and opposites from the columns of Eq. 3; moving-wall
@@ -91,6 +97,8 @@ struct orc_sim {
     double *X, *V, *W, *q, *R, *m, *I;
     unsigned char* fixed;
     double *Fh, *Th, *Fc, *Tc;
+    double *Fh_prev, *Th_prev; /* sums of Eqs. 18-19 of the previous step */
+    double *Fa, *Ta;           /* applied: mean of this and the previous step */
     double *Vh, *Wh;
     hist_list* hist;
     /* source */
@@ -369,8 +377,8 @@ static void dem_substeps(orc_sim* s) {
             }
             for (int a = 0; a < 3; ++a) {
                 Vh[a] = s->V[3 * i + a] +
-                        0.5 * dt * (s->Fc[3 * i + a] + s->Fh[3 * i + a] + g[a]) / s->m[i];
-                Wh[a] = s->W[3 * i + a] + 0.5 * dt * (s->Tc[3 * i + a] + s->Th[3 * i + a]) / s->I[i];
+                        0.5 * dt * (s->Fc[3 * i + a] + s->Fa[3 * i + a] + g[a]) / s->m[i];
+                Wh[a] = s->W[3 * i + a] + 0.5 * dt * (s->Tc[3 * i + a] + s->Ta[3 * i + a]) / s->I[i];
                 s->X[3 * i + a] += dt * Vh[a];
             }
             double* qq = &s->q[4 * i];
@@ -395,9 +403,9 @@ static void dem_substeps(orc_sim* s) {
             }
             for (int a = 0; a < 3; ++a) {
                 s->V[3 * i + a] = s->Vh[3 * i + a] +
-                                  0.5 * dt * (s->Fc[3 * i + a] + s->Fh[3 * i + a] + g[a]) / s->m[i];
+                                  0.5 * dt * (s->Fc[3 * i + a] + s->Fa[3 * i + a] + g[a]) / s->m[i];
                 s->W[3 * i + a] = s->Wh[3 * i + a] +
-                                  0.5 * dt * (s->Tc[3 * i + a] + s->Th[3 * i + a]) / s->I[i];
+                                  0.5 * dt * (s->Tc[3 * i + a] + s->Ta[3 * i + a]) / s->I[i];
             }
         }
     }
@@ -664,6 +672,10 @@ int orc_set_packing(orc_sim* s, int n, const double* X, const double* R, const d
     free(s->Tc);
     free(s->Vh);
     free(s->Wh);
+    free(s->Fh_prev);
+    free(s->Th_prev);
+    free(s->Fa);
+    free(s->Ta);
     if (s->hist) {
         for (int i = 0; i < s->np; ++i) free(s->hist[i].e);
         free(s->hist);
@@ -684,6 +696,10 @@ int orc_set_packing(orc_sim* s, int n, const double* X, const double* R, const d
     s->Tc = (double*)calloc(3 * nn, sizeof(double));
     s->Vh = (double*)calloc(3 * nn, sizeof(double));
     s->Wh = (double*)calloc(3 * nn, sizeof(double));
+    s->Fh_prev = (double*)calloc(3 * nn, sizeof(double));
+    s->Th_prev = (double*)calloc(3 * nn, sizeof(double));
+    s->Fa = (double*)calloc(3 * nn, sizeof(double));
+    s->Ta = (double*)calloc(3 * nn, sizeof(double));
     s->hist = (hist_list*)calloc(nn, sizeof(hist_list));
     for (int i = 0; i < n; ++i) {
         if (!(R[i] > 0)) return -1;
@@ -738,6 +754,12 @@ int orc_step(orc_sim* s, long long nsteps) {
         } else {
             memset(s->Fh, 0, sizeof(double) * 3 * s->np);
             memset(s->Th, 0, sizeof(double) * 3 * s->np);
+        }
+        for (int i = 0; i < 3 * s->np; ++i) {
+            s->Fa[i] = 0.5 * (s->Fh[i] + s->Fh_prev[i]);
+            s->Ta[i] = 0.5 * (s->Th[i] + s->Th_prev[i]);
+            s->Fh_prev[i] = s->Fh[i];
+            s->Th_prev[i] = s->Th[i];
         }
         dem_substeps(s);
         s->t++;
@@ -813,6 +835,10 @@ void orc_destroy(orc_sim* s) {
     free(s->Tc);
     free(s->Vh);
     free(s->Wh);
+    free(s->Fh_prev);
+    free(s->Th_prev);
+    free(s->Fa);
+    free(s->Ta);
     if (s->hist) {
         for (int i = 0; i < s->np; ++i) free(s->hist[i].e);
         free(s->hist);

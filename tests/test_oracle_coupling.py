@@ -5,8 +5,10 @@ benchmark (Section 3.2).
   moves no mass, so total mass is conserved to round-off.
 * Moving spheres in a fully periodic box: link exchange (Eq. 15) and the
   node conversions (Eqs. 16-17) move momentum between fluid and particles
-  only, so fluid + particle momentum is conserved to round-off -- this fixes
-  the signs of Eqs. 15-17 and the lever-free parts of Eqs. 18-19.
+  only.  The spheres are driven by the mean of the exchange sums of the
+  current and previous step, so fluid + sphere momentum + half the last
+  step's sum is conserved to round-off -- this fixes the signs of Eqs. 15-17
+  and the lever-free parts of Eqs. 18-19.
 * A translating and a rotating sphere feel the closed-form Stokes drag
   (Hasimoto's periodic-array correction for translation), which fixes the
   magnitude of the link force and the torque lever arms of Eq. 19.
@@ -68,7 +70,7 @@ def test_periodic_box_conserves_total_momentum(seed):
 
     def total():
         P = s.particles()
-        return _fluid_momentum(s) + (m[:, None] * P["V"]).sum(0)
+        return _fluid_momentum(s) + (m[:, None] * P["V"]).sum(0) + 0.5 * P["Fh"].sum(0)
 
     p0 = total()
     o0 = s.owner().copy()
