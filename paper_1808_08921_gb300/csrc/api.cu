@@ -1,0 +1,1145 @@
+// api.cu -- the C ABI (include/lbmdem.h): context, layout orchestration, the
+// coupled step loop (CUDA graphs of several steps), re-layouts and read-outs.
+//
+// One coupled step t -> t+1 on the context stream (Sections 2.1-2.4):
+//   map update (re-test band nodes, convert covered/uncovered nodes)
+//   collide + stream (even or odd AA kernel)
+//   link bounce-back + hydrodynamic force and torque
+//   inlet / outlet
+//   K DEM substeps (one cluster launch; also advances the device step counter)
+// Steps are captured in CUDA graphs of `graph_steps` steps starting at even t.
+// With mobile spheres the host reads back the largest displacement since the
+// last re-layout every few graphs and rebuilds the compact lattice and the
+// neighbour lists before any sphere can leave its skin.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbmdem.h"
+#include "common.cuh"
+#include "kernels.cuh"
+#include "layout.cuh"
+
+using namespace lbmdem;
+
+namespace {
+
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    ~DBuf() { release(); }
+    cudaError_t alloc(size_t count) {
+        release();
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void**)&p, sizeof(T) * count);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            n = 0;
+            return e;
+        }
+        n = count;
+        return cudaSuccess;
+    }
+    cudaError_t ensure(size_t count) { return count <= n && p ? cudaSuccess : alloc(count + count / 8); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void swap(DBuf& o) {
+        std::swap(p, o.p);
+        std::swap(n, o.n);
+    }
+};
+
+constexpr int NGROUP = 5;  // collide, links, map update, inlet/outlet, DEM
+
+}  // namespace
+
+struct lbmdem_ctx {
+    lbmdem_params p{};
+    std::string err;
+    int status_latched = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int nw = 0;
+    size_t N = 0, W = 0;
+    bool lbm = true;
+    bool have_packing = false;
+    int64_t t = 0;
+    Source src{};
+    double skin = 0.25, dem_skin = 0.5, trigger = 0.0, hard = 0.0;
+    // lattice
+    DBuf<int32_t> owner;
+    DBuf<uint8_t> deep, band;
+    DBuf<uint4> rec, rec2;
+    DBuf<uint32_t> maskB, maskB2, cntA, cntB, scan_tmp;
+    DBuf<float> f, f2;
+    DBuf<uint32_t> coord, fbits;
+    uint32_t nA = 0, nS = 0, nSpad = 0;
+    DBuf<uint32_t> band_coord, band_count;
+    DBuf<int4> band_cand;
+    uint32_t nband = 0;
+    DBuf<uint32_t> surf_count, surf_off;
+    DBuf<uint2> surf_ent;
+    DBuf<int32_t> warp_part;
+    uint32_t nwarps = 0;
+    DBuf<Flip> flip_rec;
+    DBuf<float> flip_scratch;
+    DBuf<uint8_t> flip_valid;
+    uint32_t flip_cap = 0;
+    uint32_t pA0 = 0, pA1 = 0, pB0 = 0, pB1 = 0;
+    // particles
+    int np = 0;
+    bool any_mobile = false;
+    double Rmax = 0;
+    DBuf<double> Xref, Fh, Th, Rd, Fh_prev, Th_prev;
+    DBuf<float4> Fa, Ta;
+    DBuf<float4> dX, dXc, dXb, V, Om, q, Vhb, Whb, Fc, Tc, xf;
+    DBuf<int4> org;
+    DBuf<float> R, invm, invI;
+    DBuf<uint8_t> fixed;
+    int nbmax = 48;
+    DBuf<int> nb_cnt, nb_j, nb_cnt2, nb_j2;
+    DBuf<int8_t> nb_sh, nb_sh2;
+    DBuf<float4> nb_dref, nb_ft, nb_dref2, nb_ft2;
+    CellGrid grid{};
+    DBuf<int> cell_of, cell_count, cell_start, cell_fill, cell_order;
+    // stats, probe
+    DBuf<DevStats> st;
+    DevStats* st_host = nullptr;
+    DBuf<double> probe;
+    size_t probe_cap = 0;
+    int64_t mon_step = -1;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_group;  // group of each recorded pair (pairs = ev[2k], ev[2k+1])
+    size_t ev_pairs = 0;
+    size_t gpairs = 0;                  // event pairs recorded by one graph launch
+    std::vector<int> gev_group;
+    double tm_ms[NGROUP] = {0};
+    int64_t tm_n[NGROUP] = {0};
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    int glen = 16;
+    bool gtiming = false;
+    int64_t relayouts = 0;
+    int64_t steps_until_check = 0;
+};
+
+// ------------------------------------------------------------ helpers
+
+static int fail(lbmdem_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? LBMDEM_ERR_OOM : LBMDEM_ERR_CUDA,     \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);      \
+    } while (0)
+
+static int map_status(uint32_t s) {
+    if (s & ST_UNSTABLE) return LBMDEM_ERR_UNSTABLE;
+    if (s & ST_SKIN) return LBMDEM_ERR_SKIN;
+    if (s & ST_CAPACITY) return LBMDEM_ERR_CAPACITY;
+    if (s & ST_TIMEOUT) return LBMDEM_ERR_TIMEOUT;
+    return 0;
+}
+
+static const char* status_text(int code) {
+    switch (code) {
+        case LBMDEM_ERR_UNSTABLE: return "device status: NaN/Inf in the fluid or the spheres";
+        case LBMDEM_ERR_SKIN: return "device status: a sphere moved beyond the re-layout skin";
+        case LBMDEM_ERR_CAPACITY: return "device status: a device list overflowed";
+        case LBMDEM_ERR_TIMEOUT: return "device status: a bounded wait gave up";
+    }
+    return "";
+}
+
+static Lat make_lat(lbmdem_ctx* c) {
+    Lat L{};
+    L.nx = c->p.nx;
+    L.ny = c->p.ny;
+    L.nz = c->p.nz;
+    L.nw = c->nw;
+    L.px = c->p.inlet == LBMDEM_X_PERIODIC;
+    L.nA = c->nA;
+    L.nS = c->nS;
+    L.nSpad = c->nSpad;
+    L.f = c->f.p;
+    L.rec = c->rec.p;
+    L.maskB = c->maskB.p;
+    L.coord = c->coord.p;
+    L.fbits = c->fbits.p;
+    L.owner = c->owner.p;
+    L.tau_inv = (float)(1.0 / c->p.tau);
+    L.rho_f = (float)c->p.rho_f;
+    return L;
+}
+
+static PartView make_part(lbmdem_ctx* c) {
+    PartView P{};
+    P.n = c->np;
+    P.Xref = c->Xref.p;
+    P.dX = c->dX.p;
+    P.dXc = c->dXc.p;
+    P.V = c->V.p;
+    P.W = c->Om.p;
+    P.R = c->R.p;
+    P.Rd = c->Rd.p;
+    P.org = c->org.p;
+    P.xf = c->xf.p;
+    P.Fh = c->Fh.p;
+    P.Th = c->Th.p;
+    return P;
+}
+
+static Dem make_dem(lbmdem_ctx* c) {
+    Dem D{};
+    D.n = c->np;
+    D.K = c->p.dem_substeps;
+    D.cluster = 8;
+    D.dt = 1.0f / (float)c->p.dem_substeps;
+    D.kn = (float)(2.0 * c->p.E_p / (3.0 * (1.0 - c->p.nu_p * c->p.nu_p)));
+    D.kt = (float)(2.0 * c->p.E_p / ((1.0 + c->p.nu_p) * (2.0 - c->p.nu_p)));
+    D.mu = (float)c->p.mu;
+    D.g = make_float3((float)c->p.body_force[0], (float)c->p.body_force[1], (float)c->p.body_force[2]);
+    D.nbmax = c->nbmax;
+    D.Xref = c->Xref.p;
+    D.dX = c->dX.p;
+    D.dXc = c->dXc.p;
+    D.dXb = c->dXb.p;
+    D.V = c->V.p;
+    D.W = c->Om.p;
+    D.q = c->q.p;
+    D.Vhb = c->Vhb.p;
+    D.Whb = c->Whb.p;
+    D.Fc = c->Fc.p;
+    D.Tc = c->Tc.p;
+    D.Fh = c->Fh.p;
+    D.Th = c->Th.p;
+    D.Fh_prev = c->Fh_prev.p;
+    D.Th_prev = c->Th_prev.p;
+    D.Fa = c->Fa.p;
+    D.Ta = c->Ta.p;
+    D.R = c->R.p;
+    D.invm = c->invm.p;
+    D.invI = c->invI.p;
+    D.fixed = c->fixed.p;
+    D.nb_cnt = c->nb_cnt.p;
+    D.nb_j = c->nb_j.p;
+    D.nb_dref = c->nb_dref.p;
+    D.nb_ft = c->nb_ft.p;
+    D.org = c->org.p;
+    D.xf = c->xf.p;
+    DevStats* s = c->st.p;
+    D.status = &s->status;
+    D.max_disp_bits = &s->max_disp_bits;
+    D.max_vel_bits = &s->max_vel_bits;
+    D.t_dev = &s->t;
+    D.hard_disp = (float)c->hard;
+    D.px = c->p.inlet == LBMDEM_X_PERIODIC;
+    D.Lx = c->p.nx;
+    D.Ly = c->p.ny;
+    D.Lz = c->p.nz;
+    return D;
+}
+
+static void destroy_graph(lbmdem_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+}
+
+// ------------------------------------------------------------ layout build
+
+static int build_cells(lbmdem_ctx* c) {
+    CellGrid& G = c->grid;
+    int np = c->np;
+    double h = 2.0 * c->Rmax + c->dem_skin;
+    if (h <= 0) h = 1.0;
+    int px = c->p.inlet == LBMDEM_X_PERIODIC;
+    G.px = px;
+    G.L = make_double3(c->p.nx, c->p.ny, c->p.nz);
+    if (px) {
+        G.nc.x = std::max(1, (int)floor(c->p.nx / h));
+        G.lo.x = 0;
+        G.h.x = (double)c->p.nx / G.nc.x;
+    } else {
+        double lo = -(c->Rmax + 2.0), hi = c->p.nx + c->Rmax + 2.0;
+        G.nc.x = std::max(1, (int)floor((hi - lo) / h));
+        G.lo.x = lo;
+        G.h.x = (hi - lo) / G.nc.x;
+    }
+    G.nc.y = std::max(1, (int)floor(c->p.ny / h));
+    G.h.y = (double)c->p.ny / G.nc.y;
+    G.nc.z = std::max(1, (int)floor(c->p.nz / h));
+    G.h.z = (double)c->p.nz / G.nc.z;
+    G.lo.y = G.lo.z = 0;
+    int ncell = G.nc.x * G.nc.y * G.nc.z;
+    CK(c->cell_of.ensure(np));
+    CK(c->cell_count.ensure(ncell));
+    CK(c->cell_start.ensure(ncell + 1));
+    CK(c->cell_fill.ensure(ncell));
+    CK(c->cell_order.ensure(np));
+    launch_cells(c->Xref.p, np, G, c->cell_of.p, c->cell_count.p, c->cell_start.p, c->cell_fill.p,
+                 c->cell_order.p, c->stream);
+    CK(cudaGetLastError());
+    return 0;
+}
+
+// neighbour lists from Xref; `carry` keeps the tangential history
+static int build_neighbours(lbmdem_ctx* c, bool carry) {
+    int np = c->np;
+    size_t ne = (size_t)std::max(np, 1) * c->nbmax;
+    CK(c->nb_cnt2.ensure(np));
+    CK(c->nb_j2.ensure(ne));
+    CK(c->nb_sh2.ensure(4 * ne));
+    CK(c->nb_dref2.ensure(ne));
+    CK(c->nb_ft2.ensure(ne));
+    NbBuild B{};
+    B.X = c->Xref.p;
+    B.R = c->Rd.p;
+    B.n = np;
+    B.nbmax = c->nbmax;
+    B.skin = c->dem_skin;
+    B.G = c->grid;
+    B.start = c->cell_start.p;
+    B.order = c->cell_order.p;
+    B.cnt = c->nb_cnt2.p;
+    B.nj = c->nb_j2.p;
+    B.nsh = c->nb_sh2.p;
+    B.dref = c->nb_dref2.p;
+    B.ft = c->nb_ft2.p;
+    bool have_old = carry && c->nb_cnt.p && c->nb_cnt.n >= (size_t)np;
+    B.old_cnt = have_old ? c->nb_cnt.p : nullptr;
+    B.old_j = have_old ? c->nb_j.p : nullptr;
+    B.old_sh = have_old ? c->nb_sh.p : nullptr;
+    B.old_ft = have_old ? c->nb_ft.p : nullptr;
+    B.status = &c->st.p->status;
+    launch_nb_build(B, c->stream);
+    CK(cudaGetLastError());
+    c->nb_cnt.swap(c->nb_cnt2);
+    c->nb_j.swap(c->nb_j2);
+    c->nb_sh.swap(c->nb_sh2);
+    c->nb_dref.swap(c->nb_dref2);
+    c->nb_ft.swap(c->nb_ft2);
+    return 0;
+}
+
+static int read_u32(lbmdem_ctx* c, const uint32_t* d, uint32_t* h) {
+    CK(cudaMemcpyAsync(h, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return 0;
+}
+
+// Compact lattice from Xref.  fresh: fluid at rest; else copy the populations
+// from the current layout (the state must be between an odd and an even step).
+static int build_layout(lbmdem_ctx* c, bool fresh) {
+    cudaStream_t s = c->stream;
+    int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    int px = c->p.inlet == LBMDEM_X_PERIODIC;
+    if (fresh) fill_i32(c->owner.p, OWNER_FLUID, c->N, s);
+    CK(cudaMemsetAsync(c->deep.p, 0, c->N, s));
+    CK(cudaMemsetAsync(c->band.p, 0, c->N, s));
+    PaintArgs PA{c->Xref.p, c->Rd.p, nx, ny, nz, px, c->skin, fresh ? c->owner.p : nullptr, c->deep.p,
+                 c->band.p};
+    launch_paint(PA, c->np, s);
+    CK(cudaGetLastError());
+    // words into the spare record set (the current one is needed for the copy)
+    LayoutArgs LA{nx, ny, nz, c->nw, c->owner.p, c->deep.p, c->band.p, c->rec2.p, c->maskB2.p,
+                  c->cntA.p, c->cntB.p, nullptr};
+    CK(cudaMemsetAsync(c->cntA.p, 0, sizeof(uint32_t) * (c->W + 1), s));
+    CK(cudaMemsetAsync(c->cntB.p, 0, sizeof(uint32_t) * (c->W + 1), s));
+    launch_words(LA, s);
+    exclusive_scan(c->cntA.p, c->cntA.p, c->W + 1, c->scan_tmp.p, s);
+    exclusive_scan(c->cntB.p, c->cntB.p, c->W + 1, c->scan_tmp.p, s);
+    CK(cudaGetLastError());
+    uint32_t nA = 0, nB = 0;
+    if (int r = read_u32(c, c->cntA.p + c->W, &nA)) return r;
+    if (int r = read_u32(c, c->cntB.p + c->W, &nB)) return r;
+    uint64_t nS64 = (uint64_t)nA + nB;
+    if (nS64 >= 0xffffffe0ull) return fail(c, LBMDEM_ERR_INVALID_ARG, "lattice too large");
+    uint32_t nS = (uint32_t)nS64;
+    uint32_t nSpad = std::max<uint32_t>(32u, (nS + 31u) & ~31u);
+    launch_words_bases(LA, nA, s);
+    CK(c->coord.ensure(nSpad));
+    CK(c->fbits.ensure(nSpad / 32));
+    LA.coord = c->coord.p;
+    launch_coords(LA, nA, nSpad, c->fbits.p, s);
+    CK(cudaGetLastError());
+    // populations
+    CK(c->f2.alloc((size_t)Q * nSpad));
+    CK(cudaMemsetAsync(c->f2.p, 0, sizeof(float) * Q * nSpad, s));
+    Lat Lnew = make_lat(c);
+    Lnew.nA = nA;
+    Lnew.nS = nS;
+    Lnew.nSpad = nSpad;
+    Lnew.f = c->f2.p;
+    Lnew.rec = c->rec2.p;
+    Lnew.maskB = c->maskB2.p;
+    if (!fresh && c->f.p) {
+        Lat Lold = make_lat(c);
+        launch_gather_old(Lnew, Lold, s);
+        CK(cudaGetLastError());
+    }
+    c->f.swap(c->f2);
+    c->f2.release();
+    c->rec.swap(c->rec2);
+    c->maskB.swap(c->maskB2);
+    c->nA = nA;
+    c->nS = nS;
+    c->nSpad = nSpad;
+    // band list and its candidate spheres
+    CK(cudaMemsetAsync(c->band_count.p, 0, sizeof(uint32_t), s));
+    CK(c->band_coord.ensure(1024));
+    launch_band_collect(LA, c->band_coord.p, c->band_count.p, (uint32_t)c->band_coord.n, s);
+    uint32_t nband = 0;
+    if (int r = read_u32(c, c->band_count.p, &nband)) return r;
+    if (nband > c->band_coord.n) {
+        CK(c->band_coord.alloc(nband + nband / 8));
+        CK(cudaMemsetAsync(c->band_count.p, 0, sizeof(uint32_t), s));
+        launch_band_collect(LA, c->band_coord.p, c->band_count.p, (uint32_t)c->band_coord.n, s);
+    }
+    c->nband = nband;
+    CK(c->band_cand.ensure(std::max<uint32_t>(nband, 1)));
+    if (int r = build_cells(c)) return r;
+    BandCand BC{c->Xref.p, c->Rd.p, c->skin, c->grid, c->cell_start.p, c->cell_order.p,
+                c->band_coord.p, c->band_cand.p, nband, &c->st.p->status};
+    launch_band_cand(BC, s);
+    CK(cudaGetLastError());
+    // surface lists for the link kernel
+    int np = c->np;
+    CK(c->surf_count.ensure(np + 1));
+    CK(c->surf_off.ensure(np + 1));
+    CK(cudaMemsetAsync(c->surf_count.p, 0, sizeof(uint32_t) * (np + 1), s));
+    SurfArgs SA{};
+    SA.L = make_lat(c);
+    SA.X = c->Xref.p;
+    SA.R = c->Rd.p;
+    SA.reach_extra = c->skin + 1.5;
+    SA.count = c->surf_count.p;
+    launch_surf_count(SA, np, s);
+    exclusive_scan(c->surf_count.p, c->surf_off.p, np + 1, c->scan_tmp.p, s);
+    uint32_t nent = 0;
+    if (int r = read_u32(c, c->surf_off.p + np, &nent)) return r;
+    CK(c->surf_ent.ensure(std::max<uint32_t>(nent, 32)));
+    CK(c->warp_part.ensure(std::max<uint32_t>(nent / 32, 1)));
+    SA.offset = c->surf_off.p;
+    SA.ent = c->surf_ent.p;
+    SA.warp_part = c->warp_part.p;
+    launch_surf_fill(SA, np, s);
+    CK(cudaGetLastError());
+    c->nwarps = nent / 32;
+    // conversion scratch
+    uint32_t cap = c->p.max_flips > 0 ? (uint32_t)c->p.max_flips
+                                      : std::min<uint32_t>(1u << 20, std::max<uint32_t>(4096u, nband / 8));
+    if (cap != c->flip_cap) {
+        CK(c->flip_rec.alloc(cap));
+        CK(c->flip_scratch.alloc((size_t)cap * Q * Q));
+        CK(c->flip_valid.alloc((size_t)cap * Q));
+        c->flip_cap = cap;
+    }
+    // probe plane ranges in compact order
+    c->pA0 = c->pA1 = c->pB0 = c->pB1 = 0;
+    int xp = c->p.probe_x;
+    if (xp >= 0 && xp < nx) {
+        uint4 r0, r1;
+        CK(cudaMemcpyAsync(&r0, c->rec.p + (size_t)xp * ny * c->nw, sizeof(uint4), cudaMemcpyDeviceToHost, s));
+        if (xp + 1 < nx)
+            CK(cudaMemcpyAsync(&r1, c->rec.p + (size_t)(xp + 1) * ny * c->nw, sizeof(uint4),
+                               cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        c->pA0 = r0.z;
+        c->pA1 = xp + 1 < nx ? r1.z : nA;
+        c->pB0 = r0.w;
+        c->pB1 = xp + 1 < nx ? r1.w : nS;
+    }
+    CK(cudaStreamSynchronize(s));
+    destroy_graph(c);
+    return 0;
+}
+
+// ------------------------------------------------------------ stepping
+
+static void record_pair_begin(lbmdem_ctx* c, int group, size_t& idx) {
+    idx = c->ev_pairs++;
+    while (c->ev.size() < 2 * c->ev_pairs) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev.push_back(e);
+    }
+    if (c->ev_group.size() < c->ev_pairs) c->ev_group.resize(c->ev_pairs);
+    c->ev_group[idx] = group;
+    cudaEventRecord(c->ev[2 * idx], c->stream);
+}
+
+static void record_pair_end(lbmdem_ctx* c, size_t idx) { cudaEventRecord(c->ev[2 * idx + 1], c->stream); }
+
+static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
+    cudaStream_t s = c->stream;
+    bool tm = c->timing;
+    size_t e = 0;
+    if (c->lbm) {
+        Lat L = make_lat(c);
+        PartView P = make_part(c);
+        Band B{c->band_coord.p, c->band_cand.p, c->nband};
+        FlipBuf F{c->flip_rec.p, c->flip_scratch.p, c->flip_valid.p, c->flip_cap};
+        if (tm) record_pair_begin(c, 2, e);
+        launch_map_update(L, P, B, F, c->st.p, parity == 1, parity, s);
+        if (tm) record_pair_end(c, e);
+        Mon mon{};
+        DevStats* sd = c->st.p;
+        mon.acc = sd->mon;
+        mon.umax_bits = &sd->max_u_bits;
+        mon.status = &sd->status;
+        mon.probe_sum = c->p.probe_x >= 0 ? c->probe.p : nullptr;
+        mon.t_dev = &sd->t;
+        mon.pA0 = c->pA0;
+        mon.pA1 = c->pA1;
+        mon.pB0 = c->pB0;
+        mon.pB1 = c->pB1;
+        if (monitor) {
+            cudaMemsetAsync(sd->mon, 0, sizeof(double) * 6, s);
+            cudaMemsetAsync(&sd->max_u_bits, 0, sizeof(uint32_t), s);
+        }
+        if (tm) record_pair_begin(c, 0, e);
+        launch_collide(L, mon, parity == 1, monitor, s);
+        if (tm) record_pair_end(c, e);
+        LinkLists LL{c->surf_ent.p, c->warp_part.p, c->nwarps};
+        if (tm) record_pair_begin(c, 1, e);
+        launch_links(L, P, LL, s);
+        if (tm) record_pair_end(c, e);
+        BC bc{c->p.inlet, c->p.outlet, c->src, &sd->t};
+        if (tm) record_pair_begin(c, 3, e);
+        launch_inlet_outlet(L, bc, parity == 0, s);
+        if (tm) record_pair_end(c, e);
+    }
+    Dem D = make_dem(c);
+    if (tm) record_pair_begin(c, 4, e);
+    launch_dem_step(D, false, s);
+    if (tm) record_pair_end(c, e);
+}
+
+static int collect_timing(lbmdem_ctx* c) {
+    if (c->ev_pairs == 0) return 0;
+    CK(cudaStreamSynchronize(c->stream));
+    for (size_t k = 0; k < c->ev_pairs; ++k) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
+        c->tm_ms[c->ev_group[k]] += ms;
+        c->tm_n[c->ev_group[k]] += 1;
+    }
+    c->ev_pairs = 0;
+    return 0;
+}
+
+static int ensure_probe(lbmdem_ctx* c, int64_t upto) {
+    if (c->p.probe_x < 0) return 0;
+    if ((size_t)upto <= c->probe_cap) return 0;
+    size_t cap = std::max<size_t>((size_t)upto * 2, 4096);
+    DBuf<double> nb;
+    CK(nb.alloc(2 * cap));
+    CK(cudaMemsetAsync(nb.p, 0, sizeof(double) * 2 * cap, c->stream));
+    if (c->probe.p && c->probe_cap)
+        CK(cudaMemcpyAsync(nb.p, c->probe.p, sizeof(double) * 2 * c->probe_cap, cudaMemcpyDeviceToDevice,
+                           c->stream));
+    c->probe.swap(nb);
+    nb.release();
+    c->probe_cap = cap;
+    destroy_graph(c);
+    return 0;
+}
+
+static int capture_graph(lbmdem_ctx* c) {
+    destroy_graph(c);
+    if (int r = collect_timing(c)) return r;
+    bool mon = c->p.monitor_every > 0;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < c->glen; ++k) enqueue_step(c, k & 1, mon && k == c->glen - 1);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return fail(c, LBMDEM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, LBMDEM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    c->gtiming = c->timing;
+    // event pairs recorded during capture belong to the graph: they are
+    // recorded again by every launch and read back after it
+    c->gpairs = c->ev_pairs;
+    c->gev_group.assign(c->ev_group.begin(), c->ev_group.begin() + c->gpairs);
+    c->ev_pairs = 0;
+    return 0;
+}
+
+static int relayout(lbmdem_ctx* c);
+
+static int check_and_relayout(lbmdem_ctx* c, bool& did) {
+    did = false;
+    CK(cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int code = map_status(c->st_host->status);
+    if (code) {
+        c->status_latched = code;
+        return fail(c, code, "%s", status_text(code));
+    }
+    float disp, vel;
+    uint32_t db = c->st_host->max_disp_bits, vb = c->st_host->max_vel_bits;
+    memcpy(&disp, &db, 4);
+    memcpy(&vel, &vb, 4);
+    CK(cudaMemsetAsync(&c->st.p->max_disp_bits, 0, 2 * sizeof(uint32_t), c->stream));
+    if (disp > c->trigger && (c->t % 2) == 0) {
+        if (int r = relayout(c)) return r;
+        did = true;
+        disp = 0.f;
+    }
+    double room = c->trigger - disp;
+    double v = std::max<double>(vel, 1e-9);
+    double steps = room > 0 ? room / (2.0 * v) : 1.0;
+    c->steps_until_check = (int64_t)std::max(1.0, std::min(steps, 1.0e9));
+    return 0;
+}
+
+// ------------------------------------------------------------ public API
+
+static int relayout(lbmdem_ctx* c) {
+    cudaStream_t s = c->stream;
+    launch_rebase(c->Xref.p, c->dX.p, c->dXc.p, c->np, s);
+    CK(cudaGetLastError());
+    if (int r = build_cells(c)) return r;
+    if (int r = build_neighbours(c, true)) return r;
+    if (c->lbm) {
+        if (int r = build_layout(c, false)) return r;
+    }
+    Dem D = make_dem(c);
+    launch_dem_step(D, true, s);
+    CK(cudaGetLastError());
+    c->relayouts++;
+    destroy_graph(c);
+    return 0;
+}
+
+extern "C" {
+
+void lbm_dem_default_params(lbmdem_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->nx = 64;
+    p->ny = 16;
+    p->nz = 16;
+    p->tau = 0.8;
+    p->rho_f = 1.0;
+    p->storage = LBMDEM_F32;
+    p->inlet = LBMDEM_INLET_PRESSURE;
+    p->outlet = LBMDEM_OUT_ZERO_GRAD;
+    p->dem_substeps = 10;
+    p->E_p = 10.37;
+    p->nu_p = 0.2;
+    p->mu = 0.3;
+    p->rho_p = 2.466;
+    p->probe_x = -1;
+    p->lbm_on = 1;
+    p->skin = 0.0;
+    p->dem_skin = 0.0;
+    p->monitor_every = 0;
+    p->graph_steps = 0;
+    p->max_flips = 0;
+    p->device = 0;
+    p->cuda_stream = nullptr;
+}
+
+int lbm_dem_init(const lbmdem_params* pp, lbmdem_ctx** out) {
+    lbmdem_ctx* c = nullptr;
+    if (!out) return LBMDEM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!pp) return LBMDEM_ERR_INVALID_ARG;
+    const lbmdem_params& p = *pp;
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1 || p.nx > 4096 || p.ny > 1024 || p.nz > 1024)
+        return LBMDEM_ERR_INVALID_ARG;
+    if (!(p.tau > 0.5) || !(p.rho_f > 0) || p.dem_substeps < 1) return LBMDEM_ERR_INVALID_ARG;
+    if (p.storage != LBMDEM_F32) return LBMDEM_ERR_INVALID_ARG;
+    if (p.inlet < 0 || p.inlet > 2 || p.outlet < 0 || p.outlet > 2) return LBMDEM_ERR_INVALID_ARG;
+    if (p.inlet != LBMDEM_X_PERIODIC && p.nx < 3) return LBMDEM_ERR_INVALID_ARG;
+    if (p.probe_x >= p.nx || p.probe_x < -1) return LBMDEM_ERR_INVALID_ARG;
+    if (!(p.E_p > 0) || !(p.nu_p > -1 && p.nu_p < 0.5) || !(p.mu >= 0) || !(p.rho_p > 0))
+        return LBMDEM_ERR_INVALID_ARG;
+    if (p.skin < 0 || p.dem_skin < 0 || p.graph_steps < 0 || p.graph_steps % 2 || p.max_flips < 0)
+        return LBMDEM_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= p.device || p.device < 0)
+        return LBMDEM_ERR_NO_DEVICE;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, p.device) != cudaSuccess) return LBMDEM_ERR_NO_DEVICE;
+    if (prop.major < 10) return LBMDEM_ERR_NO_DEVICE;
+    c = new lbmdem_ctx();
+    c->p = p;
+    c->lbm = p.lbm_on != 0;
+    c->skin = p.skin > 0 ? p.skin : 0.25;
+    c->dem_skin = p.dem_skin > 0 ? p.dem_skin : 0.5;
+    c->hard = std::min(c->skin, 0.5 * c->dem_skin);
+    c->trigger = 0.5 * c->hard;
+    c->glen = p.graph_steps > 0 ? p.graph_steps : 16;
+    c->nw = (p.nz + 31) / 32;
+    c->N = (size_t)p.nx * p.ny * p.nz;
+    c->W = (size_t)p.nx * p.ny * c->nw;
+    auto bail = [&](int code) {
+        lbm_dem_destroy(c);
+        return code;
+    };
+    if (cudaSetDevice(p.device) != cudaSuccess) return bail(LBMDEM_ERR_CUDA);
+    if (p.cuda_stream) {
+        c->stream = (cudaStream_t)p.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(LBMDEM_ERR_CUDA);
+        c->own_stream = true;
+    }
+    if (c->st.alloc(1) != cudaSuccess) return bail(LBMDEM_ERR_OOM);
+    if (cudaMallocHost((void**)&c->st_host, sizeof(DevStats)) != cudaSuccess) return bail(LBMDEM_ERR_OOM);
+    if (cudaMemset(c->st.p, 0, sizeof(DevStats)) != cudaSuccess) return bail(LBMDEM_ERR_CUDA);
+    if (c->lbm) {
+        if (c->owner.alloc(c->N) || c->deep.alloc(c->N) || c->band.alloc(c->N) || c->rec.alloc(c->W) ||
+            c->rec2.alloc(c->W) || c->maskB.alloc(c->W) || c->maskB2.alloc(c->W) ||
+            c->cntA.alloc(c->W + 1) || c->cntB.alloc(c->W + 1) ||
+            c->scan_tmp.alloc(scan_tmp_size(std::max(c->W + 1, (size_t)1 << 20))) ||
+            c->band_count.alloc(1))
+            return bail(LBMDEM_ERR_OOM);
+    }
+    c->src.waveform = LBMDEM_SINE;
+    c->src.amp = 0.0;
+    c->src.omega = 0.0;
+    c->src.t0 = 0.0;
+    c->src.t_n = -1;
+    *out = c;
+    return 0;
+}
+
+int lbm_dem_set_packing(lbmdem_ctx* c, int32_t n, const double* X, const double* Rh, const double* Vh,
+                        const double* Wh, const uint8_t* fixedh) {
+    if (!c) return LBMDEM_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!X || !Rh))) return fail(c, LBMDEM_ERR_INVALID_ARG, "bad packing arrays");
+    CK(cudaSetDevice(c->p.device));
+    const lbmdem_params& p = c->p;
+    int px = p.inlet == LBMDEM_X_PERIODIC;
+    double Rmax = 0, Rmin = 1e300;
+    for (int i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) {
+            if (!std::isfinite(X[3 * i + a])) return fail(c, LBMDEM_ERR_INVALID_ARG, "non-finite X[%d]", i);
+            if (Vh && !std::isfinite(Vh[3 * i + a])) return fail(c, LBMDEM_ERR_INVALID_ARG, "non-finite V");
+            if (Wh && !std::isfinite(Wh[3 * i + a])) return fail(c, LBMDEM_ERR_INVALID_ARG, "non-finite Omega");
+        }
+        if (!(Rh[i] > 0) || !std::isfinite(Rh[i])) return fail(c, LBMDEM_ERR_INVALID_ARG, "R[%d] <= 0", i);
+        Rmax = std::max(Rmax, Rh[i]);
+        Rmin = std::min(Rmin, Rh[i]);
+    }
+    // geometry limits: a node is near at most one image of a sphere, and a
+    // sphere meets each image of a neighbour through one neighbour entry
+    double lim_lbm = Rmax + c->skin + 1.5;
+    double lim_dem = 2 * Rmax + c->dem_skin;
+    double Ls[3] = {(double)p.nx, (double)p.ny, (double)p.nz};
+    for (int a = 0; a < 3; ++a) {
+        bool per = a > 0 || px;
+        if (!per || n == 0) continue;
+        if (c->lbm && 2 * lim_lbm >= Ls[a])
+            return fail(c, LBMDEM_ERR_INVALID_ARG, "R + skin + 1.5 must stay below half the periodic box (axis %d)", a);
+        if (lim_dem > Ls[a])
+            return fail(c, LBMDEM_ERR_INVALID_ARG, "2 R + dem_skin must not exceed the periodic box (axis %d)", a);
+    }
+    if (n > 0 && n <= 20000) {
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                double d2 = 0;
+                for (int a = 0; a < 3; ++a) {
+                    double d = X[3 * j + a] - X[3 * i + a];
+                    if (a > 0 || px) d -= Ls[a] * floor(d / Ls[a] + 0.5);
+                    d2 += d * d;
+                }
+                double ov = Rh[i] + Rh[j] - sqrt(d2);
+                if (ov >= std::min(Rh[i], Rh[j]))
+                    return fail(c, LBMDEM_ERR_INVALID_ARG, "spheres %d and %d overlap by %.3g", i, j, ov);
+            }
+    }
+    c->np = n;
+    c->Rmax = Rmax;
+    c->have_packing = false;
+    destroy_graph(c);
+    size_t nn = std::max(n, 1);
+    CK(c->Xref.alloc(3 * nn));
+    CK(c->Fh.alloc(3 * nn));
+    CK(c->Th.alloc(3 * nn));
+    CK(c->Fh_prev.alloc(3 * nn));
+    CK(c->Th_prev.alloc(3 * nn));
+    CK(c->Fa.alloc(nn));
+    CK(c->Ta.alloc(nn));
+    CK(c->dX.alloc(nn));
+    CK(c->dXc.alloc(nn));
+    CK(c->dXb.alloc(2 * nn));
+    CK(c->V.alloc(nn));
+    CK(c->Om.alloc(nn));
+    CK(c->q.alloc(nn));
+    CK(c->Vhb.alloc(2 * nn));
+    CK(c->Whb.alloc(2 * nn));
+    CK(c->Fc.alloc(nn));
+    CK(c->Tc.alloc(nn));
+    CK(c->xf.alloc(nn));
+    CK(c->org.alloc(nn));
+    CK(c->R.alloc(nn));
+    CK(c->Rd.alloc(nn));
+    CK(c->invm.alloc(nn));
+    CK(c->invI.alloc(nn));
+    CK(c->fixed.alloc(nn));
+    // host staging of the per-sphere constants (marshalling only)
+    std::vector<double> Xv(3 * nn, 0.0);
+    std::vector<float4> Vv(nn), Wv(nn), qv(nn), zero4(nn);
+    std::vector<float> Rv(nn, 1.f), imv(nn, 0.f), iIv(nn, 0.f);
+    std::vector<double> Rdv(nn, 1.0);
+    std::vector<uint8_t> fx(nn, 0);
+    bool mobile = false;
+    for (int i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) Xv[3 * i + a] = X[3 * i + a];
+        fx[i] = fixedh ? (fixedh[i] ? 1 : 0) : 0;
+        float v[3] = {0, 0, 0}, w[3] = {0, 0, 0};
+        if (!fx[i]) {
+            mobile = true;
+            for (int a = 0; a < 3; ++a) {
+                v[a] = Vh ? (float)Vh[3 * i + a] : 0.f;
+                w[a] = Wh ? (float)Wh[3 * i + a] : 0.f;
+            }
+        }
+        Vv[i] = make_float4(v[0], v[1], v[2], 0.f);
+        Wv[i] = make_float4(w[0], w[1], w[2], 0.f);
+        qv[i] = make_float4(1.f, 0.f, 0.f, 0.f);
+        double m = p.rho_p * 4.0 / 3.0 * M_PI * Rh[i] * Rh[i] * Rh[i];
+        Rv[i] = (float)Rh[i];
+        Rdv[i] = Rh[i];
+        imv[i] = (float)(1.0 / m);
+        iIv[i] = (float)(1.0 / (0.4 * m * Rh[i] * Rh[i]));
+    }
+    for (size_t i = 0; i < nn; ++i) zero4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    c->any_mobile = mobile;
+    cudaStream_t s = c->stream;
+    CK(cudaMemcpyAsync(c->Xref.p, Xv.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->V.p, Vv.data(), sizeof(float4) * nn, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->Om.p, Wv.data(), sizeof(float4) * nn, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->q.p, qv.data(), sizeof(float4) * nn, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->dX.p, zero4.data(), sizeof(float4) * nn, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->dXc.p, zero4.data(), sizeof(float4) * nn, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->R.p, Rv.data(), sizeof(float) * nn, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->Rd.p, Rdv.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->invm.p, imv.data(), sizeof(float) * nn, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->invI.p, iIv.data(), sizeof(float) * nn, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->fixed.p, fx.data(), nn, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(c->Fh.p, 0, sizeof(double) * 3 * nn, s));
+    CK(cudaMemsetAsync(c->Th.p, 0, sizeof(double) * 3 * nn, s));
+    CK(cudaMemsetAsync(c->Fh_prev.p, 0, sizeof(double) * 3 * nn, s));
+    CK(cudaMemsetAsync(c->Th_prev.p, 0, sizeof(double) * 3 * nn, s));
+    CK(cudaMemsetAsync(c->st.p, 0, sizeof(DevStats), s));
+    if (int r = build_cells(c)) return r;
+    if (int r = build_neighbours(c, false)) return r;
+    if (c->lbm) {
+        if (int r = build_layout(c, true)) return r;
+    }
+    c->t = 0;
+    c->mon_step = -1;
+    c->probe_cap = 0;
+    c->probe.release();
+    if (int r = ensure_probe(c, 4096)) return r;
+    Dem D = make_dem(c);
+    launch_dem_step(D, true, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int code = map_status(c->st_host->status);
+    if (code) {
+        c->status_latched = code;
+        return fail(c, code, "set_packing: %s", status_text(code));
+    }
+    c->status_latched = 0;
+    c->steps_until_check = 0;
+    c->have_packing = true;
+    c->err.clear();
+    return 0;
+}
+
+int lbm_dem_set_pressure_source(lbmdem_ctx* c, int32_t waveform, double amplitude, double omega,
+                                int64_t t_n, double t0) {
+    if (!c) return LBMDEM_ERR_INVALID_ARG;
+    if (waveform < 0 || waveform > LBMDEM_RICKER || !std::isfinite(amplitude) || !std::isfinite(omega) ||
+        !std::isfinite(t0))
+        return fail(c, LBMDEM_ERR_INVALID_ARG, "bad source");
+    c->src.waveform = waveform;
+    c->src.amp = amplitude;
+    c->src.omega = omega;
+    c->src.t_n = t_n;
+    c->src.t0 = t0;
+    destroy_graph(c);
+    return 0;
+}
+
+int lbm_dem_step(lbmdem_ctx* c, int64_t n) {
+    if (!c) return LBMDEM_ERR_INVALID_ARG;
+    if (n < 0) return fail(c, LBMDEM_ERR_INVALID_ARG, "n < 0");
+    if (!c->have_packing) return fail(c, LBMDEM_ERR_STATE, "step before set_packing");
+    if (c->status_latched) return fail(c, c->status_latched, "%s", status_text(c->status_latched));
+    CK(cudaSetDevice(c->p.device));
+    if (int r = ensure_probe(c, c->t + n + 1)) return r;
+    bool checks = c->any_mobile;
+    while (n > 0) {
+        if (checks && c->steps_until_check <= 0) {
+            bool did;
+            if (int r = check_and_relayout(c, did)) return r;
+        }
+        int64_t room = checks ? c->steps_until_check : n;
+        bool use_graph = (c->t % 2 == 0) && n >= c->glen && room >= c->glen;
+        if (use_graph) {
+            if (!c->gexec || c->gtiming != c->timing) {
+                if (int r = capture_graph(c)) return r;
+            }
+            CK(cudaGraphLaunch(c->gexec, c->stream));
+            if (c->p.monitor_every > 0) c->mon_step = c->t + c->glen - 1;
+            c->t += c->glen;
+            n -= c->glen;
+            c->steps_until_check -= c->glen;
+            if (c->timing) {
+                c->ev_pairs = c->gpairs;
+                for (size_t k = 0; k < c->gpairs; ++k) c->ev_group[k] = c->gev_group[k];
+                if (int r = collect_timing(c)) return r;
+            }
+        } else {
+            bool mon = c->p.monitor_every > 0 && ((c->t + 1) % c->p.monitor_every == 0);
+            size_t pairs0 = c->ev_pairs;
+            enqueue_step(c, (int)(c->t & 1), mon);
+            CK(cudaGetLastError());
+            if (mon) c->mon_step = c->t;
+            c->t += 1;
+            n -= 1;
+            c->steps_until_check -= 1;
+            if (c->timing && c->ev_pairs > pairs0) {
+                if (int r = collect_timing(c)) return r;
+            }
+        }
+    }
+    return 0;
+}
+
+int lbm_dem_relayout(lbmdem_ctx* c) {
+    if (!c) return LBMDEM_ERR_INVALID_ARG;
+    if (!c->have_packing) return fail(c, LBMDEM_ERR_STATE, "relayout before set_packing");
+    if (c->t % 2) return fail(c, LBMDEM_ERR_STATE, "relayout needs an even step count");
+    CK(cudaSetDevice(c->p.device));
+    if (int r = relayout(c)) return r;
+    CK(cudaMemsetAsync(&c->st.p->max_disp_bits, 0, 2 * sizeof(uint32_t), c->stream));
+    c->steps_until_check = 0;
+    return lbm_dem_status(c);
+}
+
+int lbm_dem_status(lbmdem_ctx* c) {
+    if (!c) return LBMDEM_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int code = map_status(c->st_host->status);
+    if (code) c->status_latched = code;
+    return code;
+}
+
+__global__ void k_particles_out(Dem D, const double* Fh, const double* Th, double* X, double* V,
+                                double* W, double* q, double* F, double* T) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D.n) return;
+    float4 d = D.dX[i], c = D.dXc[i], v = D.V[i], w = D.W[i], qq = D.q[i];
+    X[3 * i] = D.Xref[3 * i] + (double)d.x - (double)c.x;
+    X[3 * i + 1] = D.Xref[3 * i + 1] + (double)d.y - (double)c.y;
+    X[3 * i + 2] = D.Xref[3 * i + 2] + (double)d.z - (double)c.z;
+    V[3 * i] = v.x;
+    V[3 * i + 1] = v.y;
+    V[3 * i + 2] = v.z;
+    W[3 * i] = w.x;
+    W[3 * i + 1] = w.y;
+    W[3 * i + 2] = w.z;
+    q[4 * i] = qq.x;
+    q[4 * i + 1] = qq.y;
+    q[4 * i + 2] = qq.z;
+    q[4 * i + 3] = qq.w;
+    for (int a = 0; a < 3; ++a) {
+        F[3 * i + a] = Fh[3 * i + a];
+        T[3 * i + a] = Th[3 * i + a];
+    }
+}
+
+int lbm_dem_read_particles(lbmdem_ctx* c, double* X, double* V, double* Om, double* quat, double* F_hyd,
+                           double* T_hyd) {
+    if (!c) return LBMDEM_ERR_INVALID_ARG;
+    if (!c->have_packing) return fail(c, LBMDEM_ERR_STATE, "no packing");
+    if (c->np == 0) return 0;
+    CK(cudaSetDevice(c->p.device));
+    size_t n = c->np;
+    DBuf<double> buf;
+    CK(buf.alloc(19 * n));
+    double* d = buf.p;
+    Dem D = make_dem(c);
+    k_particles_out<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(D, c->Fh.p, c->Th.p, d, d + 3 * n,
+                                                                      d + 6 * n, d + 9 * n, d + 13 * n,
+                                                                      d + 16 * n);
+    CK(cudaGetLastError());
+    std::vector<double> h(19 * n);
+    CK(cudaMemcpyAsync(h.data(), d, sizeof(double) * 19 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (X) memcpy(X, h.data(), sizeof(double) * 3 * n);
+    if (V) memcpy(V, h.data() + 3 * n, sizeof(double) * 3 * n);
+    if (Om) memcpy(Om, h.data() + 6 * n, sizeof(double) * 3 * n);
+    if (quat) memcpy(quat, h.data() + 9 * n, sizeof(double) * 4 * n);
+    if (F_hyd) memcpy(F_hyd, h.data() + 13 * n, sizeof(double) * 3 * n);
+    if (T_hyd) memcpy(T_hyd, h.data() + 16 * n, sizeof(double) * 3 * n);
+    return lbm_dem_status(c);
+}
+
+int lbm_dem_read_fields(lbmdem_ctx* c, double* rho, double* u, uint8_t* solid) {
+    if (!c) return LBMDEM_ERR_INVALID_ARG;
+    if (!c->have_packing) return fail(c, LBMDEM_ERR_STATE, "no packing");
+    if (!c->lbm) return fail(c, LBMDEM_ERR_STATE, "fluid is off");
+    CK(cudaSetDevice(c->p.device));
+    size_t N = c->N;
+    DBuf<double> dr, du;
+    DBuf<uint8_t> ds;
+    if (rho) CK(dr.alloc(N));
+    if (u) CK(du.alloc(3 * N));
+    if (solid) CK(ds.alloc(N));
+    Lat L = make_lat(c);
+    launch_read_fields(L, (c->t & 1) == 1, rho ? dr.p : nullptr, u ? du.p : nullptr, solid ? ds.p : nullptr,
+                       c->stream);
+    CK(cudaGetLastError());
+    if (rho) CK(cudaMemcpyAsync(rho, dr.p, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+    if (u) CK(cudaMemcpyAsync(u, du.p, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->stream));
+    if (solid) CK(cudaMemcpyAsync(solid, ds.p, N, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return lbm_dem_status(c);
+}
+
+__global__ void k_probe_out(const double* sums, int64_t n, double rho_f, double* out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double cnt = sums[2 * k + 1];
+    out[k] = cnt > 0 ? rho_f + sums[2 * k] / cnt : nan("");
+}
+
+int lbm_dem_read_probe(lbmdem_ctx* c, double* trace, int64_t max_len, int64_t* len) {
+    if (!c) return LBMDEM_ERR_INVALID_ARG;
+    if (len) *len = c->p.probe_x >= 0 && c->lbm ? c->t : 0;
+    if (c->p.probe_x < 0 || !c->lbm || c->t == 0 || !trace || max_len <= 0) return lbm_dem_status(c);
+    CK(cudaSetDevice(c->p.device));
+    int64_t n = std::min<int64_t>(max_len, c->t);
+    DBuf<double> d;
+    CK(d.alloc(n));
+    k_probe_out<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->probe.p, n, c->p.rho_f, d.p);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(trace, d.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return lbm_dem_status(c);
+}
+
+__global__ void k_monitors_out(const DevStats* s, double rho_f, double* out) {
+    if (threadIdx.x || blockIdx.x) return;
+    out[0] = rho_f * s->mon[4] + s->mon[0];
+    out[1] = s->mon[1];
+    out[2] = s->mon[2];
+    out[3] = s->mon[3];
+    out[4] = sqrt((double)__uint_as_float(s->max_u_bits));
+}
+
+int lbm_dem_read_monitors(lbmdem_ctx* c, double out[6]) {
+    if (!c || !out) return LBMDEM_ERR_INVALID_ARG;
+    if (!c->lbm) return fail(c, LBMDEM_ERR_STATE, "fluid is off");
+    DBuf<double> d;
+    CK(d.alloc(6));
+    k_monitors_out<<<1, 1, 0, c->stream>>>(c->st.p, c->p.rho_f, d.p);
+    CK(cudaMemcpyAsync(out, d.p, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    out[5] = (double)c->mon_step;
+    return lbm_dem_status(c);
+}
+
+int lbm_dem_read_counters(lbmdem_ctx* c, int64_t out[9]) {
+    if (!c || !out) return LBMDEM_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int64_t fluid = 0;
+    if (c->lbm && c->nS) {
+        // fluid nodes now: popcount of the compact fluid bits (host reduce of a
+        // device array; counters are diagnostics, not part of the step)
+        std::vector<uint32_t> fb(c->nSpad / 32);
+        CK(cudaMemcpy(fb.data(), c->fbits.p, sizeof(uint32_t) * fb.size(), cudaMemcpyDeviceToHost));
+        for (uint32_t w : fb) fluid += __builtin_popcount(w);
+    }
+    int64_t nb = 0;
+    if (c->np) {
+        std::vector<int> cnt(c->np);
+        CK(cudaMemcpy(cnt.data(), c->nb_cnt.p, sizeof(int) * c->np, cudaMemcpyDeviceToHost));
+        for (int v : cnt) nb += v;
+    }
+    out[0] = (int64_t)c->N;
+    out[1] = c->nS;
+    out[2] = fluid;
+    out[3] = c->nband;
+    out[4] = (int64_t)c->nwarps * 32;
+    out[5] = nb;
+    out[6] = c->t;
+    out[7] = c->relayouts;
+    out[8] = (int64_t)c->st_host->flips_total;
+    return 0;
+}
+
+int lbm_dem_set_timing(lbmdem_ctx* c, int32_t enable) {
+    if (!c) return LBMDEM_ERR_INVALID_ARG;
+    if (int r = collect_timing(c)) return r;
+    c->timing = enable != 0;
+    for (int g = 0; g < NGROUP; ++g) {
+        c->tm_ms[g] = 0;
+        c->tm_n[g] = 0;
+    }
+    destroy_graph(c);
+    return 0;
+}
+
+int lbm_dem_read_timing(lbmdem_ctx* c, double ms[5], int64_t launches[5]) {
+    if (!c) return LBMDEM_ERR_INVALID_ARG;
+    if (int r = collect_timing(c)) return r;
+    for (int g = 0; g < NGROUP; ++g) {
+        if (ms) ms[g] = c->tm_ms[g];
+        if (launches) launches[g] = c->tm_n[g];
+        c->tm_ms[g] = 0;
+        c->tm_n[g] = 0;
+    }
+    return 0;
+}
+
+const char* lbm_dem_last_error(const lbmdem_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void lbm_dem_destroy(lbmdem_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    destroy_graph(c);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->st_host) cudaFreeHost(c->st_host);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaSetDevice(c->p.device);
+    delete c;  // device buffers are released by their destructors
+}
+
+}  // extern "C"

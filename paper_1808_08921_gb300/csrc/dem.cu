@@ -1,0 +1,515 @@
+// dem.cu -- the solid phase (Section 2.2, Eqs. 9-12).
+//
+//  * k_dem_step: one launch per LBM step, one thread-block cluster (<= 8
+//    CTAs, co-scheduled), one thread per sphere.  It runs the K velocity-
+//    Verlet substeps of length 1/K with the hydrodynamic force and torque of
+//    the step held fixed: kick + drift of the own sphere, one cluster barrier,
+//    then the contact forces of the own sphere from its neighbour list and
+//    the closing kick.  Positions and half-step velocities read by the
+//    neighbours are double-buffered by substep parity, so one barrier per
+//    substep suffices.  Each pair is evaluated by both spheres with mirror-
+//    exact arithmetic, so the two forces are exact negatives and no atomics
+//    are needed.  The hydrodynamic force and torque that drive a sphere are
+//    the mean of the exchange sums of this and the previous LBM step (the
+//    half-way bounce-back force alternates from step to step; the two-step
+//    mean of Ladd's momentum-exchange method keeps the explicit coupling of
+//    light spheres stable).
+//  * neighbour lists: uniform cells of size >= 2 R_max + skin over the
+//    periodic y, z box; every periodic image is a separate entry (a sphere in
+//    a narrow box can touch two images of the same neighbour).  Rebuilt only
+//    at re-layouts; the tangential history is carried over by (j, image).
+//
+// Positions are X = Xref (FP64, fixed between re-layouts) + dX (FP32 with a
+// Kahan compensation term), so the substep loop needs no FP64 arithmetic.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "layout.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace lbmdem {
+
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 crossf(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// Contact forces on sphere i (Eqs. 11-12): Hertz normal force, incremental
+// Mindlin tangential force from the half-step relative velocity at the
+// contact point, previous tangential force projected on the current tangent
+// plane, Coulomb cap.  dt_inc = 0 evaluates without tangential increment.
+__device__ void contact_forces(const Dem& D, int i, int b, float dt_inc, float3& F, float3& T) {
+    float4 xi4 = __ldcg(&D.dXb[b * D.n + i]);
+    float3 xi = f3(xi4), vi = f3(__ldcg(&D.Vhb[b * D.n + i])), wi = f3(__ldcg(&D.Whb[b * D.n + i]));
+    float Ri = D.R[i];
+    F = make_float3(0.f, 0.f, 0.f);
+    T = make_float3(0.f, 0.f, 0.f);
+    int cnt = D.nb_cnt[i];
+    for (int k = 0; k < cnt; ++k) {
+        size_t e = (size_t)i * D.nbmax + k;
+        int j = D.nb_j[e];
+        float4 dr = D.nb_dref[e];
+        float3 xj = f3(__ldcg(&D.dXb[b * D.n + j]));
+        float3 dl = make_float3(xj.x - xi.x, xj.y - xi.y, xj.z - xi.z);
+        float3 d = make_float3(dr.x + dl.x, dr.y + dl.y, dr.z + dl.z);
+        float Rj = D.R[j];
+        float cut = Ri + Rj;
+        // cut^2 - |d|^2 without cancellation: e0 - 2 dref.dl - dl.dl
+        float qd = dr.w - (2.f * (dr.x * dl.x + dr.y * dl.y + dr.z * dl.z) +
+                           (dl.x * dl.x + dl.y * dl.y + dl.z * dl.z));
+        if (!(qd > 0.f)) {
+            D.nb_ft[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        float dist = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+        float delta = qd / (cut + dist);
+        float3 n = make_float3(d.x / dist, d.y / dist, d.z / dist);
+        float Rs = Ri * Rj / (Ri + Rj);
+        float sq = sqrtf(Rs * delta);
+        float fn = D.kn * sq * delta;
+        float ai = Ri - 0.5f * delta, aj = Rj - 0.5f * delta;
+        float3 ri = make_float3(ai * n.x, ai * n.y, ai * n.z);
+        float3 rj = make_float3(-(aj * n.x), -(aj * n.y), -(aj * n.z));
+        float3 vj = f3(__ldcg(&D.Vhb[b * D.n + j])), wj = f3(__ldcg(&D.Whb[b * D.n + j]));
+        float3 cwj = crossf(wj, rj), cwi = crossf(wi, ri);
+        float3 vr = make_float3((vj.x + cwj.x) - (vi.x + cwi.x), (vj.y + cwj.y) - (vi.y + cwi.y),
+                                (vj.z + cwj.z) - (vi.z + cwi.z));
+        float vn = vr.x * n.x + vr.y * n.y + vr.z * n.z;
+        float3 vt = make_float3(vr.x - vn * n.x, vr.y - vn * n.y, vr.z - vn * n.z);
+        float4 h = D.nb_ft[e];
+        float hn = h.x * n.x + h.y * n.y + h.z * n.z;
+        float kdt = D.kt * sq * dt_inc;
+        float3 ft = make_float3(h.x - hn * n.x + kdt * vt.x, h.y - hn * n.y + kdt * vt.y,
+                                h.z - hn * n.z + kdt * vt.z);
+        float ftm = sqrtf(ft.x * ft.x + ft.y * ft.y + ft.z * ft.z);
+        float cap = D.mu * fn;
+        if (ftm > cap) {
+            float sc = cap / ftm;
+            ft = make_float3(ft.x * sc, ft.y * sc, ft.z * sc);
+        }
+        D.nb_ft[e] = make_float4(ft.x, ft.y, ft.z, 0.f);
+        float3 Fk = make_float3(-fn * n.x + ft.x, -fn * n.y + ft.y, -fn * n.z + ft.z);
+        float3 Tk = crossf(ri, Fk);
+        F.x += Fk.x;
+        F.y += Fk.y;
+        F.z += Fk.z;
+        T.x += Tk.x;
+        T.y += Tk.y;
+        T.z += Tk.z;
+    }
+}
+
+__global__ void k_dem_step(Dem D, int init_only) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int nth = gridDim.x * blockDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const float dt = D.dt;
+    if (init_only) {
+        for (int i = tid; i < D.n; i += nth) {
+            D.dXb[i] = D.dX[i];
+            D.Vhb[i] = D.V[i];
+            D.Whb[i] = D.W[i];
+        }
+        cl.sync();
+        for (int i = tid; i < D.n; i += nth) {
+            float3 F, T;
+            contact_forces(D, i, 0, 0.f, F, T);
+            D.Fc[i] = make_float4(F.x, F.y, F.z, 0.f);
+            D.Tc[i] = make_float4(T.x, T.y, T.z, 0.f);
+        }
+    }
+    if (!init_only) {
+        for (int i = tid; i < D.n; i += nth) {
+            double f[3], t[3];
+            for (int a = 0; a < 3; ++a) {
+                f[a] = D.Fh[3 * i + a];
+                t[a] = D.Th[3 * i + a];
+            }
+            D.Fa[i] = make_float4((float)(0.5 * (f[0] + D.Fh_prev[3 * i])), (float)(0.5 * (f[1] + D.Fh_prev[3 * i + 1])),
+                                  (float)(0.5 * (f[2] + D.Fh_prev[3 * i + 2])), 0.f);
+            D.Ta[i] = make_float4((float)(0.5 * (t[0] + D.Th_prev[3 * i])), (float)(0.5 * (t[1] + D.Th_prev[3 * i + 1])),
+                                  (float)(0.5 * (t[2] + D.Th_prev[3 * i + 2])), 0.f);
+            for (int a = 0; a < 3; ++a) {
+                D.Fh_prev[3 * i + a] = f[a];
+                D.Th_prev[3 * i + a] = t[a];
+            }
+        }
+    }
+    for (int s = 0; s < (init_only ? 0 : D.K); ++s) {
+        const int b = s & 1;
+        for (int i = tid; i < D.n; i += nth) {
+            float4 dx = D.dX[i];
+            float4 vh, wh;
+            if (D.fixed[i]) {
+                vh = wh = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                float4 fc = D.Fc[i], tc = D.Tc[i], v = D.V[i], w = D.W[i];
+                float im = D.invm[i], iI = D.invI[i];
+                float4 fa = D.Fa[i], ta = D.Ta[i];
+                float fhx = fa.x, fhy = fa.y, fhz = fa.z;
+                float thx = ta.x, thy = ta.y, thz = ta.z;
+                vh = make_float4(v.x + 0.5f * dt * (fc.x + fhx + D.g.x) * im,
+                                 v.y + 0.5f * dt * (fc.y + fhy + D.g.y) * im,
+                                 v.z + 0.5f * dt * (fc.z + fhz + D.g.z) * im, 0.f);
+                wh = make_float4(w.x + 0.5f * dt * (tc.x + thx) * iI, w.y + 0.5f * dt * (tc.y + thy) * iI,
+                                 w.z + 0.5f * dt * (tc.z + thz) * iI, 0.f);
+                // drift with Kahan-compensated FP32 accumulation
+                float4 c = D.dXc[i];
+                float yx = dt * vh.x - c.x, yy = dt * vh.y - c.y, yz = dt * vh.z - c.z;
+                float tx = dx.x + yx, ty = dx.y + yy, tz = dx.z + yz;
+                c = make_float4((tx - dx.x) - yx, (ty - dx.y) - yy, (tz - dx.z) - yz, 0.f);
+                dx = make_float4(tx, ty, tz, 0.f);
+                D.dX[i] = dx;
+                D.dXc[i] = c;
+                // quaternion, q <- normalize(q + dt/2 (0, W) q)
+                float4 q = D.q[i];
+                float dq0 = -(wh.x * q.y + wh.y * q.z + wh.z * q.w);
+                float3 wxv = crossf(f3(wh), make_float3(q.y, q.z, q.w));
+                float4 dq = make_float4(dq0, q.x * wh.x + wxv.x, q.x * wh.y + wxv.y, q.x * wh.z + wxv.z);
+                q = make_float4(q.x + 0.5f * dt * dq.x, q.y + 0.5f * dt * dq.y, q.z + 0.5f * dt * dq.z,
+                                q.w + 0.5f * dt * dq.w);
+                float nq = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+                D.q[i] = make_float4(q.x * nq, q.y * nq, q.z * nq, q.w * nq);
+            }
+            D.dXb[b * D.n + i] = dx;
+            D.Vhb[b * D.n + i] = vh;
+            D.Whb[b * D.n + i] = wh;
+        }
+        cl.sync();
+        for (int i = tid; i < D.n; i += nth) {
+            if (D.fixed[i]) {
+                D.V[i] = D.W[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                continue;
+            }
+            float3 F, T;
+            contact_forces(D, i, b, dt, F, T);
+            D.Fc[i] = make_float4(F.x, F.y, F.z, 0.f);
+            D.Tc[i] = make_float4(T.x, T.y, T.z, 0.f);
+            float4 vh = D.Vhb[b * D.n + i], wh = D.Whb[b * D.n + i];
+            float im = D.invm[i], iI = D.invI[i];
+            float4 fa = D.Fa[i], ta = D.Ta[i];
+            float fhx = fa.x, fhy = fa.y, fhz = fa.z;
+            float thx = ta.x, thy = ta.y, thz = ta.z;
+            D.V[i] = make_float4(vh.x + 0.5f * dt * (F.x + fhx + D.g.x) * im,
+                                 vh.y + 0.5f * dt * (F.y + fhy + D.g.y) * im,
+                                 vh.z + 0.5f * dt * (F.z + fhz + D.g.z) * im, 0.f);
+            D.W[i] = make_float4(wh.x + 0.5f * dt * (T.x + thx) * iI, wh.y + 0.5f * dt * (T.y + thy) * iI,
+                                 wh.z + 0.5f * dt * (T.z + thz) * iI, 0.f);
+        }
+    }
+    // outputs of the step: lattice frame of every sphere, displacement and
+    // speed maxima for the re-layout decision, NaN / skin checks
+    float dmax = 0.f, vmax = 0.f;
+    uint32_t bad = 0;
+    for (int i = tid; i < D.n; i += nth) {
+        float4 dx = D.dX[i], c = D.dXc[i], v = D.V[i];
+        double X0 = D.Xref[3 * i] + (double)dx.x - (double)c.x;
+        double X1 = D.Xref[3 * i + 1] + (double)dx.y - (double)c.y;
+        double X2 = D.Xref[3 * i + 2] + (double)dx.z - (double)c.z;
+        int4 o = make_int4((int)floor(D.Xref[3 * i]), (int)floor(D.Xref[3 * i + 1]),
+                           (int)floor(D.Xref[3 * i + 2]), 0);
+        D.org[i] = o;
+        D.xf[i] = make_float4((float)(X0 - o.x), (float)(X1 - o.y), (float)(X2 - o.z), 0.f);
+        float dd = sqrtf(dx.x * dx.x + dx.y * dx.y + dx.z * dx.z);
+        float vv = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+        if (!(dd == dd) || !(vv == vv) || isinf(dd) || isinf(vv)) bad |= ST_UNSTABLE;
+        else if (dd >= D.hard_disp) bad |= ST_SKIN;
+        dmax = fmaxf(dmax, dd);
+        vmax = fmaxf(vmax, vv);
+    }
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        dmax = fmaxf(dmax, __shfl_xor_sync(full, dmax, o));
+        vmax = fmaxf(vmax, __shfl_xor_sync(full, vmax, o));
+        bad |= __shfl_xor_sync(full, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (dmax > 0.f) atomicMax(D.max_disp_bits, __float_as_uint(dmax));
+        if (vmax > 0.f) atomicMax(D.max_vel_bits, __float_as_uint(vmax));
+        if (bad) atomicOr(D.status, bad);
+    }
+    cl.sync();
+    if (tid == 0 && !init_only) *D.t_dev += 1ull;
+}
+
+void launch_dem_step(const Dem& D, bool init_only, cudaStream_t s) {
+    int C = D.cluster;
+    int T = 256;
+    if (D.n <= 256) {
+        C = 1;
+        T = D.n <= 32 ? 32 : ((D.n + 31) / 32) * 32;
+    } else if (D.n > C * 256) {
+        T = (D.n + C - 1) / C;
+        T = ((T + 31) / 32) * 32;
+        if (T > 1024) T = 1024;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(T, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_dem_step, D, init_only ? 1 : 0);
+}
+
+// ------------------------------------------------------------ neighbour lists
+
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__device__ __forceinline__ int floormod(int a, int b) { return a - floordiv(a, b) * b; }
+
+// Cell of a position: periodic axes use the wrapped coordinate and return
+// the wrap count k (X = X_wrapped + k L); the x axis clamps when not periodic.
+__device__ __forceinline__ int cell_axis(double X, double lo, double h, int nc, double L, int periodic,
+                                         int& k) {
+    if (periodic) {
+        k = (int)floor(X / L);
+        double xw = X - k * L;
+        int c = (int)floor(xw / h);
+        return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+    }
+    k = 0;
+    int c = (int)floor((X - lo) / h);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+__global__ void k_cell_count(const double* X, int n, CellGrid G, int* cell_of, int* count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int kx, ky, kz;
+    int cx_ = cell_axis(X[3 * i], G.lo.x, G.h.x, G.nc.x, G.L.x, G.px, kx);
+    int cy_ = cell_axis(X[3 * i + 1], 0.0, G.h.y, G.nc.y, G.L.y, 1, ky);
+    int cz_ = cell_axis(X[3 * i + 2], 0.0, G.h.z, G.nc.z, G.L.z, 1, kz);
+    int c = (cx_ * G.nc.y + cy_) * G.nc.z + cz_;
+    cell_of[i] = c;
+    atomicAdd(&count[c], 1);
+}
+
+__global__ void k_cell_scan_serial(const int* count, int* start, int* fill, int ncell) {
+    // cell counts are small (a few thousand cells); one thread is enough and
+    // keeps the order deterministic
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int s = 0;
+        for (int c = 0; c < ncell; ++c) {
+            start[c] = s;
+            fill[c] = s;
+            s += count[c];
+        }
+        start[ncell] = s;
+    }
+}
+
+__global__ void k_cell_fill(const int* cell_of, int n, int* fill, int* order) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int slot = atomicAdd(&fill[cell_of[i]], 1);
+    order[slot] = i;
+}
+
+// Per sphere: all (j, image) within R_i + R_j + skin, sorted by (j, image),
+// tangential history copied from the previous list where the key matches.
+__global__ void k_nb_build(NbBuild B) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.n) return;
+    const CellGrid& G = B.G;
+    double Xi[3] = {B.X[3 * i], B.X[3 * i + 1], B.X[3 * i + 2]};
+    int ki[3];
+    int ci[3];
+    ci[0] = cell_axis(Xi[0], G.lo.x, G.h.x, G.nc.x, G.L.x, G.px, ki[0]);
+    ci[1] = cell_axis(Xi[1], 0.0, G.h.y, G.nc.y, G.L.y, 1, ki[1]);
+    ci[2] = cell_axis(Xi[2], 0.0, G.h.z, G.nc.z, G.L.z, 1, ki[2]);
+    int nc[3] = {G.nc.x, G.nc.y, G.nc.z};
+    int per[3] = {G.px, 1, 1};
+    double L[3] = {G.L.x, G.L.y, G.L.z};
+    size_t base = (size_t)i * B.nbmax;
+    int cnt = 0;
+    double Ri = B.R[i];
+    for (int dx = -1; dx <= 1; ++dx) {
+        int ux = ci[0] + dx;
+        int wx = ux, sx = 0;
+        if (per[0]) {
+            wx = floormod(ux, nc[0]);
+            sx = floordiv(ux, nc[0]);
+        } else if (ux < 0 || ux >= nc[0]) {
+            continue;
+        }
+        for (int dy = -1; dy <= 1; ++dy) {
+            int uy = ci[1] + dy, wy = floormod(uy, nc[1]), sy = floordiv(uy, nc[1]);
+            for (int dz = -1; dz <= 1; ++dz) {
+                int uz = ci[2] + dz, wz = floormod(uz, nc[2]), sz = floordiv(uz, nc[2]);
+                int c = (wx * nc[1] + wy) * nc[2] + wz;
+                for (int a = B.start[c]; a < B.start[c + 1]; ++a) {
+                    int j = B.order[a];
+                    if (j == i) continue;
+                    int kj[3];
+                    cell_axis(B.X[3 * j], G.lo.x, G.h.x, G.nc.x, G.L.x, G.px, kj[0]);
+                    cell_axis(B.X[3 * j + 1], 0.0, G.h.y, G.nc.y, G.L.y, 1, kj[1]);
+                    cell_axis(B.X[3 * j + 2], 0.0, G.h.z, G.nc.z, G.L.z, 1, kj[2]);
+                    int s[3] = {per[0] ? sx - kj[0] + ki[0] : 0, sy - kj[1] + ki[1], sz - kj[2] + ki[2]};
+                    double d[3];
+                    for (int q = 0; q < 3; ++q) d[q] = (B.X[3 * j + q] + s[q] * L[q]) - Xi[q];
+                    double cut = Ri + B.R[j] + B.skin;
+                    double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (dd >= cut * cut) continue;
+                    if (cnt >= B.nbmax) {
+                        atomicOr(B.status, ST_CAPACITY);
+                        continue;
+                    }
+                    size_t e = base + cnt++;
+                    B.nj[e] = j;
+                    B.nsh[4 * e] = (int8_t)s[0];
+                    B.nsh[4 * e + 1] = (int8_t)s[1];
+                    B.nsh[4 * e + 2] = (int8_t)s[2];
+                    B.nsh[4 * e + 3] = 0;
+                    // the overlap is later formed from e0 = (R_i + R_j)^2 - |dref|^2,
+                    // taken here in FP64 from the unrounded offset, so FP32 never
+                    // cancels two ~2R numbers (nor carries dref's rounding)
+                    double c2 = Ri + B.R[j];
+                    double e0 = c2 * c2 - dd;
+                    B.dref[e] = make_float4((float)d[0], (float)d[1], (float)d[2], (float)e0);
+                }
+            }
+        }
+    }
+    // insertion sort by (j, sx, sy, sz)
+    auto key = [&](size_t e) -> long long {
+        return ((long long)B.nj[e] << 24) | ((long long)(B.nsh[4 * e] + 8) << 16) |
+               ((long long)(B.nsh[4 * e + 1] + 8) << 8) | (long long)(B.nsh[4 * e + 2] + 8);
+    };
+    for (int a = 1; a < cnt; ++a) {
+        size_t ea = base + a;
+        long long ka = key(ea);
+        int j = B.nj[ea];
+        int8_t sh[4] = {B.nsh[4 * ea], B.nsh[4 * ea + 1], B.nsh[4 * ea + 2], 0};
+        float4 dr = B.dref[ea];
+        int b = a - 1;
+        while (b >= 0 && key(base + b) > ka) {
+            size_t eb = base + b, eb1 = base + b + 1;
+            B.nj[eb1] = B.nj[eb];
+            for (int q = 0; q < 4; ++q) B.nsh[4 * eb1 + q] = B.nsh[4 * eb + q];
+            B.dref[eb1] = B.dref[eb];
+            --b;
+        }
+        size_t e = base + b + 1;
+        B.nj[e] = j;
+        for (int q = 0; q < 4; ++q) B.nsh[4 * e + q] = sh[q];
+        B.dref[e] = dr;
+    }
+    // carry the tangential history over
+    int oc = B.old_cnt ? B.old_cnt[i] : 0;
+    for (int a = 0; a < cnt; ++a) {
+        size_t e = base + a;
+        float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int b = 0; b < oc; ++b) {
+            size_t o = base + b;
+            if (B.old_j[o] == B.nj[e] && B.old_sh[4 * o] == B.nsh[4 * e] &&
+                B.old_sh[4 * o + 1] == B.nsh[4 * e + 1] && B.old_sh[4 * o + 2] == B.nsh[4 * e + 2]) {
+                h = B.old_ft[o];
+                break;
+            }
+        }
+        B.ft[e] = h;
+    }
+    B.cnt[i] = cnt;
+}
+
+
+void launch_cells(const double* X, int n, const CellGrid& G, int* cell_of, int* count, int* start,
+                  int* fill, int* order, cudaStream_t s) {
+    int ncell = G.nc.x * G.nc.y * G.nc.z;
+    cudaMemsetAsync(count, 0, sizeof(int) * ncell, s);
+    if (n > 0) k_cell_count<<<(n + 255) / 256, 256, 0, s>>>(X, n, G, cell_of, count);
+    k_cell_scan_serial<<<1, 1, 0, s>>>(count, start, fill, ncell);
+    if (n > 0) k_cell_fill<<<(n + 255) / 256, 256, 0, s>>>(cell_of, n, fill, order);
+}
+
+void launch_nb_build(const NbBuild& B, cudaStream_t s) {
+    if (B.n > 0) k_nb_build<<<(B.n + 127) / 128, 128, 0, s>>>(B);
+}
+
+// Spheres whose surface may reach a band node before the next re-layout
+// (|y - Xref| < R + skin, all images), ascending, at most 4.
+__global__ void k_band_cand(BandCand B) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= B.n) return;
+    const CellGrid& G = B.G;
+    int x, y, z;
+    unpack_coord(B.coord[k], x, y, z);
+    double P[3] = {(double)x, (double)y, (double)z};
+    int kk[3], ci[3];
+    ci[0] = cell_axis(P[0], G.lo.x, G.h.x, G.nc.x, G.L.x, G.px, kk[0]);
+    ci[1] = cell_axis(P[1], 0.0, G.h.y, G.nc.y, G.L.y, 1, kk[1]);
+    ci[2] = cell_axis(P[2], 0.0, G.h.z, G.nc.z, G.L.z, 1, kk[2]);
+    int nc[3] = {G.nc.x, G.nc.y, G.nc.z};
+    double L[3] = {G.L.x, G.L.y, G.L.z};
+    int per[3] = {G.px, 1, 1};
+    int c4[4] = {-1, -1, -1, -1};
+    int nfound = 0;
+    for (int dx = -1; dx <= 1; ++dx) {
+        int ux = ci[0] + dx, wx = ux;
+        if (per[0]) wx = floormod(ux, nc[0]);
+        else if (ux < 0 || ux >= nc[0]) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int wy = floormod(ci[1] + dy, nc[1]);
+            for (int dz = -1; dz <= 1; ++dz) {
+                int wz = floormod(ci[2] + dz, nc[2]);
+                int c = (wx * nc[1] + wy) * nc[2] + wz;
+                for (int a = B.start[c]; a < B.start[c + 1]; ++a) {
+                    int p = B.order[a];
+                    bool dup = false;
+                    for (int q = 0; q < nfound; ++q) dup |= c4[q] == p;
+                    if (dup) continue;
+                    double d2 = 0;
+                    for (int q = 0; q < 3; ++q) {
+                        double d = P[q] - B.X[3 * p + q];
+                        if (per[q]) d -= L[q] * floor(d / L[q] + 0.5);
+                        d2 += d * d;
+                    }
+                    double r = B.R[p] + B.skin;
+                    if (d2 >= r * r) continue;
+                    if (nfound >= 4) {
+                        atomicOr(B.status, ST_CAPACITY);
+                        continue;
+                    }
+                    // insert sorted
+                    int q = nfound++;
+                    while (q > 0 && c4[q - 1] > p) {
+                        c4[q] = c4[q - 1];
+                        --q;
+                    }
+                    c4[q] = p;
+                }
+            }
+        }
+    }
+    B.cand[k] = make_int4(c4[0], c4[1], c4[2], c4[3]);
+}
+
+void launch_band_cand(const BandCand& B, cudaStream_t s) {
+    if (B.n > 0) k_band_cand<<<(B.n + 255) / 256, 256, 0, s>>>(B);
+}
+
+__global__ void k_rebase(double* Xref, float4* dX, float4* dXc, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 d = dX[i], c = dXc[i];
+    Xref[3 * i] += (double)d.x - (double)c.x;
+    Xref[3 * i + 1] += (double)d.y - (double)c.y;
+    Xref[3 * i + 2] += (double)d.z - (double)c.z;
+    dX[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    dXc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+void launch_rebase(double* Xref, float4* dX, float4* dXc, int n, cudaStream_t s) {
+    if (n > 0) k_rebase<<<(n + 255) / 256, 256, 0, s>>>(Xref, dX, dXc, n);
+}
+
+}  // namespace lbmdem

@@ -1,0 +1,118 @@
+// kernels.cuh -- launch interfaces between the host orchestration (api.cu)
+// and the kernel translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace lbmdem {
+
+// Fused monitors of the collide kernels.
+struct Mon {
+    double* acc;                    // [5] sum drho, sum j, fluid count (FP64)
+    uint32_t* umax_bits;            // max |u|^2 as float bits
+    uint32_t* status;
+    double* probe_sum;              // [2 * capacity] (sum drho, count) per step, or null
+    const unsigned long long* t_dev;
+    uint32_t pA0, pA1, pB0, pB1;    // compact index ranges of the probe plane
+};
+
+struct Source {
+    int waveform;
+    double amp, omega, t0;
+    long long t_n;
+};
+
+struct BC {
+    int inlet, outlet;
+    Source src;
+    const unsigned long long* t_dev;
+};
+
+// Per-particle surface lists for the link kernel: entries {cidx, coord},
+// each particle's run padded to a multiple of 32 (one warp = one particle).
+struct LinkLists {
+    const uint2* ent;
+    const int32_t* warp_part;
+    uint32_t nwarps;
+};
+
+// Nodes whose solid/fluid status can change before the next re-layout.
+struct Band {
+    const uint32_t* coord;  // packed x, y, z
+    const int4* cand;       // up to 4 sphere indices, ascending, -1 padded
+    uint32_t n;
+};
+
+struct Flip {
+    uint32_t coord;
+    int32_t old_owner, new_owner;
+    uint32_t pad;
+};
+
+struct FlipBuf {
+    Flip* rec;
+    float* scratch;   // [cap][19][19]
+    uint8_t* valid;   // [cap][19]
+    uint32_t cap;
+};
+
+// DEM state (Section 2.2).
+struct Dem {
+    int n, K, cluster;
+    float dt;                // 1 / K
+    float kn, kt, mu;        // Eqs. 11-12 prefactors
+    float3 g;                // body force
+    int nbmax;
+    // per particle
+    const double* Xref;
+    float4* dX;              // canonical displacement since re-layout
+    float4* dXc;             // Kahan compensation
+    float4* dXb;             // [2][n] double buffer read by the force phase
+    float4* V;
+    float4* W;
+    float4* q;
+    float4* Vhb;             // [2][n]
+    float4* Whb;             // [2][n]
+    float4* Fc;              // contact force (persistent across steps)
+    float4* Tc;
+    const double* Fh;        // hydrodynamic force/torque sums of this step (Eqs. 18-19)
+    const double* Th;
+    double* Fh_prev;         // the sums of the previous step
+    double* Th_prev;
+    float4* Fa;              // applied: mean of this and the previous step
+    float4* Ta;
+    const float* R;
+    const float* invm;
+    const float* invI;
+    const uint8_t* fixed;
+    // neighbour list
+    const int* nb_cnt;
+    const int* nb_j;
+    const float4* nb_dref;   // xyz: X_ref_j + shift - X_ref_i, w: (R_i+R_j)^2 - |xyz|^2
+    float4* nb_ft;           // tangential history (force on i)
+    // outputs for the lattice kernels
+    int4* org;
+    float4* xf;
+    uint32_t* status;
+    uint32_t* max_disp_bits;
+    uint32_t* max_vel_bits;
+    unsigned long long* t_dev;   // incremented at the end of the step
+    float hard_disp;             // displacement at which the layout is invalid
+    int px;
+    double Lx, Ly, Lz;
+};
+
+// lattice.cu
+void launch_collide(const Lat& L, const Mon& mon, bool odd, bool monitor, cudaStream_t s);
+void launch_inlet_outlet(const Lat& L, const BC& bc, bool after_even, cudaStream_t s);
+void launch_read_fields(const Lat& L, bool after_even, double* rho, double* u, uint8_t* solid,
+                        cudaStream_t s);
+
+// coupling.cu
+void launch_links(const Lat& L, const PartView& P, const LinkLists& B, cudaStream_t s);
+void launch_map_update(const Lat& L, const PartView& P, const Band& band, const FlipBuf& F,
+                       DevStats* st, bool after_even, int step_parity, cudaStream_t s);
+
+// dem.cu
+void launch_dem_step(const Dem& D, bool init_only, cudaStream_t s);
+}  // namespace lbmdem

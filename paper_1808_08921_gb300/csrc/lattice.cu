@@ -1,0 +1,358 @@
+// lattice.cu -- fluid kernels on the compact AA lattice:
+//   * collide+stream, even and odd parity (Section 2.1, Eqs. 4-8), with the
+//     probe-plane density and the FP64 mass/momentum totals fused in;
+//   * pressure inlet with the oscillating density and the outlet
+//     (Section 2.4, Eq. 25, Table 2);
+//   * read-out of rho and u (Eq. 7) for any parity.
+// Populations are stored as deviations g = f - w rho_f; every formula below is
+// the paper's written in g (the weights sum to one, and sum_m w_m c_m = 0).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace lbmdem {
+
+static_assert(cx(opp(7)) == -cx(7) && cy(opp(7)) == -cy(7), "opp");
+
+// Eq. 4 with the equilibrium of Eq. 6 and the moments of Eq. 7, on deviations.
+// Returns the moments of the pre-collision state.
+__device__ __forceinline__ void bgk(float g[Q], float tau_inv, float rho_f, float& drho, float& jx,
+                                    float& jy, float& jz) {
+    drho = 0.f;
+    jx = jy = jz = 0.f;
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+        drho += g[m];
+        if (cx(m)) jx += cx(m) > 0 ? g[m] : -g[m];
+        if (cy(m)) jy += cy(m) > 0 ? g[m] : -g[m];
+        if (cz(m)) jz += cz(m) > 0 ? g[m] : -g[m];
+    }
+    float rho = rho_f + drho;
+    float ir = 1.0f / rho;
+    float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+    float uu15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+    float om = 1.0f - tau_inv;
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+        float cu = (float)cx(m) * ux + (float)cy(m) * uy + (float)cz(m) * uz;
+        float geq = wt(m) * (drho + rho * (3.0f * cu + 4.5f * cu * cu - uu15));
+        g[m] = om * g[m] + tau_inv * geq;
+    }
+}
+
+struct MonAcc {
+    float drho, jx, jy, jz, umax2, cnt;
+    float pdrho, pcnt;  // probe plane
+    int bad;
+};
+
+__device__ __forceinline__ void mon_add(MonAcc& a, float drho, float jx, float jy, float jz,
+                                        float rho_f) {
+    a.drho += drho;
+    a.cnt += 1.f;
+    a.jx += jx;
+    a.jy += jy;
+    a.jz += jz;
+    float ir = 1.0f / (rho_f + drho);
+    float u2 = (jx * jx + jy * jy + jz * jz) * ir * ir;
+    a.umax2 = fmaxf(a.umax2, u2);
+    if (!(drho == drho) || !(u2 == u2)) a.bad = 1;
+}
+
+// Warp + block reduction of the monitors, one FP64 atomic per block per
+// quantity; the probe sums use warp-aggregated atomics.
+template <bool MON>
+__device__ __forceinline__ void mon_flush(const MonAcc& a, const Mon& mon, bool probe_any) {
+    const unsigned full = 0xffffffffu;
+    if (mon.probe_sum != nullptr) {
+        if (__any_sync(full, a.pcnt > 0.f)) {
+            float s = a.pdrho, c = a.pcnt;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                s += __shfl_xor_sync(full, s, o);
+                c += __shfl_xor_sync(full, c, o);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                unsigned long long t = *mon.t_dev;
+                atomicAdd(&mon.probe_sum[2 * t], (double)s);
+                atomicAdd(&mon.probe_sum[2 * t + 1], (double)c);
+            }
+        }
+    }
+    if (!MON) return;
+    __shared__ double sh[6][32];
+    double v[5] = {a.drho, a.jx, a.jy, a.jz, a.cnt};
+    float um = a.umax2;
+    int bad = a.bad;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[k] += __shfl_xor_sync(full, v[k], o);
+        um = fmaxf(um, __shfl_xor_sync(full, um, o));
+        bad |= __shfl_xor_sync(full, bad, o);
+    }
+    int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        for (int k = 0; k < 5; ++k) sh[k][wid] = v[k];
+        sh[5][wid] = (double)um;
+        if (bad) atomicOr(mon.status, ST_UNSTABLE);
+    }
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        double r[6];
+        for (int k = 0; k < 6; ++k) r[k] = lane < nw ? sh[k][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            for (int k = 0; k < 5; ++k) r[k] += __shfl_xor_sync(full, r[k], o);
+            r[5] = fmax(r[5], __shfl_xor_sync(full, r[5], o));
+        }
+        if (lane == 0) {
+            for (int k = 0; k < 5; ++k) atomicAdd(&mon.acc[k], r[k]);
+            atomicMax(mon.umax_bits, __float_as_uint((float)r[5]));
+        }
+    }
+}
+
+// Even step: node-local.  Each thread owns 4 consecutive compact nodes and
+// moves them with 128-bit loads and stores; solid nodes inside a quad are
+// processed harmlessly (their slots are never read while they are solid).
+template <bool MON>
+__global__ void __launch_bounds__(256) k_collide_even(Lat L, Mon mon) {
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t i0 = t * 4u;
+    MonAcc a = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    bool active = i0 < L.nS;
+    uint32_t bits = 0;
+    if (active) {
+        bits = (L.fbits[i0 >> 5] >> (i0 & 31)) & 0xfu;
+        active = bits != 0;
+    }
+    if (active) {
+        float4 v[Q];
+#pragma unroll
+        for (int m = 0; m < Q; ++m)
+            v[m] = __ldcs(reinterpret_cast<const float4*>(L.f + (size_t)m * L.nSpad + i0));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float g[Q];
+#pragma unroll
+            for (int m = 0; m < Q; ++m) g[m] = (&v[m].x)[k];
+            float drho, jx, jy, jz;
+            bgk(g, L.tau_inv, L.rho_f, drho, jx, jy, jz);
+#pragma unroll
+            for (int m = 0; m < Q; ++m) (&v[opp(m)].x)[k] = g[m];
+            if ((bits >> k) & 1u) {
+                if (MON) mon_add(a, drho, jx, jy, jz, L.rho_f);
+                uint32_t i = i0 + k;
+                if ((i >= mon.pA0 && i < mon.pA1) || (i >= mon.pB0 && i < mon.pB1)) {
+                    a.pdrho += drho;
+                    a.pcnt += 1.f;
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < Q; ++m)
+            __stcs(reinterpret_cast<float4*>(L.f + (size_t)m * L.nSpad + i0), v[m]);
+    }
+    mon_flush<MON>(a, mon, true);
+}
+
+// Odd step: node x gathers direction m from slot opp(m) of x - c_m (or from
+// its own slot m when x - c_m is solid or outside), collides, and scatters
+// direction m to slot m of x + c_m (or its own slot opp(m)).  Each thread
+// reads and writes the same 19 locations, so the update is in place.
+template <bool MON>
+__global__ void __launch_bounds__(256) k_collide_odd(Lat L, Mon mon) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    MonAcc a = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    bool active = i < L.nS && fluid_bit(L, i);
+    if (active) {
+        int x, y, z;
+        unpack_coord(__ldcs(&L.coord[i]), x, y, z);
+        uint32_t nb[Q - 1];  // compact index of x + c_m, or NONE
+#pragma unroll
+        for (int m = 0; m < Q - 1; ++m) nb[m] = fluid_index(L, x, y, z, cx(m), cy(m), cz(m));
+        float g[Q];
+#pragma unroll
+        for (int m = 0; m < Q - 1; ++m) {
+            uint32_t s = nb[opp(m)];
+            g[m] = s != NONE ? L.f[(size_t)opp(m) * L.nSpad + s] : L.f[(size_t)m * L.nSpad + i];
+        }
+        g[18] = L.f[(size_t)18 * L.nSpad + i];
+        float drho, jx, jy, jz;
+        bgk(g, L.tau_inv, L.rho_f, drho, jx, jy, jz);
+#pragma unroll
+        for (int m = 0; m < Q - 1; ++m) {
+            uint32_t d = nb[m];
+            if (d != NONE)
+                L.f[(size_t)m * L.nSpad + d] = g[m];
+            else
+                L.f[(size_t)opp(m) * L.nSpad + i] = g[m];
+        }
+        L.f[(size_t)18 * L.nSpad + i] = g[18];
+        if (MON) mon_add(a, drho, jx, jy, jz, L.rho_f);
+        if ((i >= mon.pA0 && i < mon.pA1) || (i >= mon.pB0 && i < mon.pB1)) {
+            a.pdrho += drho;
+            a.pcnt += 1.f;
+        }
+    }
+    mon_flush<MON>(a, mon, true);
+}
+
+void launch_collide(const Lat& L, const Mon& mon, bool odd, bool monitor, cudaStream_t s) {
+    if (L.nS == 0) return;
+    if (!odd) {
+        uint32_t threads = (L.nS + 3) / 4;
+        uint32_t blocks = (threads + 255) / 256;
+        if (monitor)
+            k_collide_even<true><<<blocks, 256, 0, s>>>(L, mon);
+        else
+            k_collide_even<false><<<blocks, 256, 0, s>>>(L, mon);
+    } else {
+        uint32_t blocks = (L.nS + 255) / 256;
+        if (monitor)
+            k_collide_odd<true><<<blocks, 256, 0, s>>>(L, mon);
+        else
+            k_collide_odd<false><<<blocks, 256, 0, s>>>(L, mon);
+    }
+}
+
+// ------------------------------------------------------------ inlet / outlet
+
+// Eq. 25 and Table 2 at time t (steps completed), in FP64 (evaluated once
+// per block).
+__device__ double source_drho(const Source& S, unsigned long long t) {
+    if (S.t_n >= 0 && (long long)t > S.t_n) return 0.0;
+    double ph = S.omega * (double)t;
+    switch (S.waveform) {
+        case 0: return S.amp * sin(ph);
+        case 1: return S.amp * (1.0 - cos(ph));
+        case 2: return S.amp;
+        case 3: {
+            double a = 0.5 * S.omega * ((double)t - S.t0);  // pi f (t - t0), f = omega / 2 pi
+            return S.amp * (1.0 - 2.0 * a * a) * exp(-a * a);
+        }
+    }
+    return 0.0;
+}
+
+// Section 2.4, x-normal D3Q19 pressure face on deviations.  side 0: inlet
+// (unknown c_x = +1), side 1: outlet (unknown c_x = -1).  Indices are the
+// paper's d (1-based) minus one.
+__device__ __forceinline__ void pressure_face(float g[Q], float drho_b, int side) {
+    float rest = g[18] + g[2] + g[3] + g[4] + g[5] + g[14] + g[15] + g[16] + g[17];
+    float Ny = 0.5f * (g[2] + g[14] + g[15] - g[3] - g[16] - g[17]);
+    float Nz = 0.5f * (g[4] + g[14] + g[16] - g[5] - g[15] - g[17]);
+    if (side == 0) {
+        float rux = drho_b - (rest + 2.f * (g[1] + g[10] + g[11] + g[12] + g[13]));
+        g[0] = g[1] + rux * (1.f / 3.f);
+        g[6] = g[11] + rux * (1.f / 6.f) - Ny;
+        g[7] = g[10] + rux * (1.f / 6.f) + Ny;
+        g[8] = g[13] + rux * (1.f / 6.f) - Nz;
+        g[9] = g[12] + rux * (1.f / 6.f) + Nz;
+    } else {
+        float rux = (rest + 2.f * (g[0] + g[6] + g[7] + g[8] + g[9])) - drho_b;
+        g[1] = g[0] - rux * (1.f / 3.f);
+        g[11] = g[6] - rux * (1.f / 6.f) + Ny;
+        g[10] = g[7] - rux * (1.f / 6.f) - Ny;
+        g[13] = g[8] - rux * (1.f / 6.f) + Nz;
+        g[12] = g[9] - rux * (1.f / 6.f) - Nz;
+    }
+}
+
+template <bool AFTER_EVEN>
+__global__ void k_inlet_outlet(Lat L, BC bc) {
+    __shared__ float s_drho;
+    if (threadIdx.x == 0) s_drho = (float)source_drho(bc.src, *bc.t_dev + 1ull);
+    __syncthreads();
+    int plane = L.ny * L.nz;
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2 * plane) return;
+    int side = k >= plane;
+    int yz = side ? k - plane : k;
+    int y = yz / L.nz, z = yz - y * L.nz;
+    int x = side ? L.nx - 1 : 0;
+    bool fl;
+    uint32_t i = stored_index(L, x, y, z, fl);
+    if (!fl || i == NONE) return;
+    if (side == 0) {
+        if (bc.inlet != 0) return;
+        float g[Q];
+#pragma unroll
+        for (int m = 0; m < Q; ++m)
+            if (cx(m) <= 0) g[m] = *pop_loc(L, AFTER_EVEN, x, y, z, i, m);
+        pressure_face(g, s_drho, 0);
+#pragma unroll
+        for (int m = 0; m < Q; ++m)
+            if (cx(m) > 0) L.f[(size_t)m * L.nSpad + i] = g[m];  // source outside: own slot
+    } else if (bc.outlet == 0) {
+        bool ufl;
+        uint32_t u = stored_index(L, x - 1, y, z, ufl);
+        if (!ufl || u == NONE) return;
+#pragma unroll
+        for (int m = 0; m < Q; ++m)
+            if (cx(m) < 0) L.f[(size_t)m * L.nSpad + i] = *pop_loc(L, AFTER_EVEN, x - 1, y, z, u, m);
+    } else if (bc.outlet == 1) {
+        float g[Q];
+#pragma unroll
+        for (int m = 0; m < Q; ++m)
+            if (cx(m) >= 0) g[m] = *pop_loc(L, AFTER_EVEN, x, y, z, i, m);
+        pressure_face(g, 0.f, 1);
+#pragma unroll
+        for (int m = 0; m < Q; ++m)
+            if (cx(m) < 0) L.f[(size_t)m * L.nSpad + i] = g[m];
+    }
+}
+
+void launch_inlet_outlet(const Lat& L, const BC& bc, bool after_even, cudaStream_t s) {
+    if (L.px) return;
+    if (bc.inlet != 0 && bc.outlet > 1) return;
+    int n = 2 * L.ny * L.nz;
+    int blocks = (n + 127) / 128;
+    if (after_even)
+        k_inlet_outlet<true><<<blocks, 128, 0, s>>>(L, bc);
+    else
+        k_inlet_outlet<false><<<blocks, 128, 0, s>>>(L, bc);
+}
+
+// ------------------------------------------------------------ read-out
+
+__global__ void k_read_fields(Lat L, bool after_even, double* rho, double* u, uint8_t* solid) {
+    size_t N = (size_t)L.nx * L.ny * L.nz;
+    size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    int z = (int)(n % L.nz);
+    size_t r = n / L.nz;
+    int y = (int)(r % L.ny);
+    int x = (int)(r / L.ny);
+    bool fl;
+    uint32_t i = stored_index(L, x, y, z, fl);
+    fl = fl && i != NONE;
+    if (solid) solid[n] = fl ? 0 : 1;
+    double d = 0, jx = 0, jy = 0, jz = 0;
+    if (fl) {
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            double g = (double)*pop_loc(L, after_even, x, y, z, i, m);
+            d += g;
+            jx += cx(m) * g;
+            jy += cy(m) * g;
+            jz += cz(m) * g;
+        }
+    }
+    double rr = fl ? (double)L.rho_f + d : 0.0;
+    if (rho) rho[n] = rr;
+    if (u) {
+        u[n] = fl ? jx / rr : 0.0;
+        u[N + n] = fl ? jy / rr : 0.0;
+        u[2 * N + n] = fl ? jz / rr : 0.0;
+    }
+}
+
+void launch_read_fields(const Lat& L, bool after_even, double* rho, double* u, uint8_t* solid,
+                        cudaStream_t s) {
+    size_t N = (size_t)L.nx * L.ny * L.nz;
+    k_read_fields<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(L, after_even, rho, u, solid);
+}
+
+}  // namespace lbmdem

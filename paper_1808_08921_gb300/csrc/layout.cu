@@ -1,0 +1,357 @@
+// layout.cu -- building the compact lattice from the sphere positions.
+//
+// Run at set_packing and at every re-layout (when some sphere has moved a
+// good part of the skin since the last one).  Steps:
+//   1. paint: for every sphere, every node of its bounding box (all periodic
+//      images) is tested with the exact FP64 rule |y - X|^2 < R^2 shared with
+//      the map update; the owner is the lowest covering index (atomicMin).
+//      Only set_packing paints owners: after step t the map belongs to the
+//      positions of that step's map update, one DEM update behind the
+//      current ones, so a re-layout keeps the maintained map (the next map
+//      update converts what the newer positions cover or uncover).
+//      Nodes deeper than `skin` inside a sphere are flagged "deep" (never
+//      stored); nodes within `skin` of a surface are flagged "band" (re-tested
+//      every step).  The inlet/outlet planes are never solid.
+//   2. word masks and counts per 32-node word; exclusive scans give the
+//      compact indices (region A = fluid now, region B = stored solid).
+//   3. compact coordinates, fluid bits, band list with candidate spheres,
+//      per-sphere surface lists for the link kernel (warp-padded), and, on a
+//      re-layout, the populations copied from the old compact order.
+#include "common.cuh"
+#include "kernels.cuh"
+#include "layout.cuh"
+
+namespace lbmdem {
+
+__global__ void k_fill_i32(int32_t* p, int32_t v, size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+void fill_i32(int32_t* p, int32_t v, size_t n, cudaStream_t s) {
+    if (n) k_fill_i32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, v, n);
+}
+
+// ------------------------------------------------------------ scan
+
+// exclusive scan of 1024-element tiles (256 threads x 4), tile sums out
+__global__ void k_scan_tile(const uint32_t* in, uint32_t* out, uint32_t* sums, size_t n) {
+    __shared__ uint32_t sh[256];
+    size_t base = (size_t)blockIdx.x * 1024;
+    uint32_t v[4];
+    uint32_t tot = 0;
+    for (int k = 0; k < 4; ++k) {
+        size_t i = base + threadIdx.x * 4 + k;
+        v[k] = i < n ? in[i] : 0u;
+        tot += v[k];
+    }
+    sh[threadIdx.x] = tot;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+        uint32_t a = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0u;
+        __syncthreads();
+        sh[threadIdx.x] += a;
+        __syncthreads();
+    }
+    uint32_t run = sh[threadIdx.x] - tot;
+    for (int k = 0; k < 4; ++k) {
+        size_t i = base + threadIdx.x * 4 + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 255) sums[blockIdx.x] = sh[255];
+}
+
+__global__ void k_scan_add(uint32_t* out, const uint32_t* sums, size_t n) {
+    size_t i = (size_t)blockIdx.x * 1024 + threadIdx.x * 4;
+    uint32_t a = sums[blockIdx.x];
+    for (int k = 0; k < 4; ++k)
+        if (i + k < n) out[i + k] += a;
+}
+
+// out = exclusive scan of in (may alias); tmp needs scan_tmp_size(n) words.
+void exclusive_scan(const uint32_t* in, uint32_t* out, size_t n, uint32_t* tmp, cudaStream_t s) {
+    if (n == 0) return;
+    size_t tiles = (n + 1023) / 1024;
+    uint32_t* sums = tmp;
+    k_scan_tile<<<(unsigned)tiles, 256, 0, s>>>(in, out, sums, n);
+    if (tiles > 1) {
+        exclusive_scan(sums, sums, tiles, tmp + tiles, s);
+        k_scan_add<<<(unsigned)tiles, 256, 0, s>>>(out, sums, n);
+    }
+}
+
+size_t scan_tmp_size(size_t n) {
+    size_t t = 0;
+    while (n > 1) {
+        n = (n + 1023) / 1024;
+        t += n;
+    }
+    return t + 1;
+}
+
+// ------------------------------------------------------------ painting
+
+__device__ __forceinline__ int wrapi(int a, int L) {
+    int r = a % L;
+    return r < 0 ? r + L : r;
+}
+
+__global__ void k_paint(PaintArgs A) {
+    int p = blockIdx.x;
+    double X0 = A.X[3 * p], X1 = A.X[3 * p + 1], X2 = A.X[3 * p + 2];
+    double R = A.R[p];
+    double reach = R + A.skin + 1.0;
+    int x0 = (int)ceil(X0 - reach), x1 = (int)floor(X0 + reach);
+    int y0 = (int)ceil(X1 - reach), y1 = (int)floor(X1 + reach);
+    int z0 = (int)ceil(X2 - reach), z1 = (int)floor(X2 + reach);
+    int ex = x1 - x0 + 1, ey = y1 - y0 + 1, ez = z1 - z0 + 1;
+    long long vol = (long long)ex * ey * ez;
+    double Rin = R - A.skin, Rout = R + A.skin;
+    for (long long t = threadIdx.x; t < vol; t += blockDim.x) {
+        int zi = z0 + (int)(t % ez);
+        long long r = t / ez;
+        int yi = y0 + (int)(r % ey);
+        int xi = x0 + (int)(r / ey);
+        int x;
+        if (A.px) {
+            x = wrapi(xi, A.nx);
+        } else {
+            if (xi <= 0 || xi >= A.nx - 1) continue;  // boundary planes stay fluid
+            x = xi;
+        }
+        int y = wrapi(yi, A.ny), z = wrapi(zi, A.nz);
+        double ax = (double)xi - X0, ay = (double)yi - X1, az = (double)zi - X2;
+        size_t li = ((size_t)x * A.ny + y) * A.nz + z;
+        if (A.owner && inside_exact(ax, ay, az, R)) atomicMin(&A.owner[li], p);
+        double d2 = ax * ax + ay * ay + az * az;
+        if (Rin > 0 && d2 < Rin * Rin) A.deep[li] = 1;
+        if (d2 < Rout * Rout && (Rin <= 0 || d2 >= Rin * Rin)) A.band[li] = 1;
+    }
+}
+
+// word masks: maskF = maskA = stored fluid, maskB = stored solid
+__global__ void k_words(LayoutArgs A) {
+    size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t W = (size_t)A.nx * A.ny * A.nw;
+    if (w >= W) return;
+    int wz = (int)(w % A.nw);
+    size_t line = w / A.nw;
+    uint32_t mA = 0, mB = 0;
+    for (int b = 0; b < 32; ++b) {
+        int z = wz * 32 + b;
+        if (z >= A.nz) break;
+        size_t li = line * A.nz + z;
+        bool fluid = A.owner[li] == OWNER_FLUID;
+        if (A.deep[li] && !fluid) continue;
+        if (fluid)
+            mA |= 1u << b;
+        else
+            mB |= 1u << b;
+    }
+    A.rec[w] = make_uint4(mA, mA, 0u, 0u);
+    A.maskB[w] = mB;
+    A.cntA[w] = __popc(mA);
+    A.cntB[w] = __popc(mB);
+}
+
+__global__ void k_words_bases(LayoutArgs A, uint32_t nA) {
+    size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t W = (size_t)A.nx * A.ny * A.nw;
+    if (w >= W) return;
+    A.rec[w].z = A.cntA[w];
+    A.rec[w].w = nA + A.cntB[w];
+}
+
+__global__ void k_coords(LayoutArgs A) {
+    size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t W = (size_t)A.nx * A.ny * A.nw;
+    if (w >= W) return;
+    int wz = (int)(w % A.nw);
+    size_t line = w / A.nw;
+    int y = (int)(line % A.ny), x = (int)(line / A.ny);
+    uint4 r = A.rec[w];
+    uint32_t mB = A.maskB[w];
+    uint32_t ia = r.z, ib = r.w;
+    for (int b = 0; b < 32; ++b) {
+        uint32_t bit = 1u << b;
+        int z = wz * 32 + b;
+        if (r.y & bit) A.coord[ia++] = pack_coord(x, y, z);
+        if (mB & bit) A.coord[ib++] = pack_coord(x, y, z);
+    }
+}
+
+__global__ void k_fbits(uint32_t* fbits, uint32_t nA, uint32_t nwords) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nwords) return;
+    uint32_t lo = k * 32;
+    uint32_t v;
+    if (lo + 32 <= nA) v = 0xffffffffu;
+    else if (lo >= nA) v = 0u;
+    else v = (1u << (nA - lo)) - 1u;
+    fbits[k] = v;
+}
+
+// re-layout: copy the natural populations (state between an odd and an even
+// step: population m of node i sits in slot m of i) into the new order
+__global__ void k_gather_old(Lat Lnew, Lat Lold) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Lnew.nA) return;
+    int x, y, z;
+    unpack_coord(Lnew.coord[i], x, y, z);
+    bool fl;
+    uint32_t o = stored_index(Lold, x, y, z, fl);
+    if (o == NONE) return;
+#pragma unroll
+    for (int m = 0; m < Q; ++m) Lnew.f[(size_t)m * Lnew.nSpad + i] = Lold.f[(size_t)m * Lold.nSpad + o];
+}
+
+// band nodes: compact list of (coord) via atomics; candidates found later
+__global__ void k_band_collect(LayoutArgs A, uint32_t* band_coord, uint32_t* count, uint32_t cap) {
+    size_t li = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t N = (size_t)A.nx * A.ny * A.nz;
+    if (li >= N || !A.band[li]) return;
+    int z = (int)(li % A.nz);
+    size_t r = li / A.nz;
+    int y = (int)(r % A.ny), x = (int)(r / A.ny);
+    uint32_t k = atomicAdd(count, 1u);
+    if (k < cap) band_coord[k] = pack_coord(x, y, z);
+}
+
+// surface-node lists: every stored node within R + skin + sqrt(2) of a
+// sphere (all neighbours that the sphere can own before the next re-layout)
+__device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, long long t, int x0, int y0, int z0,
+                                          int ey, int ez, uint32_t& cidx, uint32_t& coord) {
+    int zi = z0 + (int)(t % ez);
+    long long r = t / ez;
+    int yi = y0 + (int)(r % ey);
+    int xi = x0 + (int)(r / ey);
+    int x;
+    if (A.L.px) x = wrapi(xi, A.L.nx);
+    else {
+        if (xi < 0 || xi >= A.L.nx) return false;
+        x = xi;
+    }
+    int y = wrapi(yi, A.L.ny), z = wrapi(zi, A.L.nz);
+    double ax = (double)xi - A.X[3 * p], ay = (double)yi - A.X[3 * p + 1], az = (double)zi - A.X[3 * p + 2];
+    double reach = A.R[p] + A.reach_extra;
+    if (ax * ax + ay * ay + az * az >= reach * reach) return false;
+    bool fl;
+    uint32_t ci = stored_index(A.L, x, y, z, fl);
+    if (ci == NONE) return false;
+    cidx = ci;
+    coord = pack_coord(x, y, z);
+    return true;
+}
+
+__global__ void k_surf_count(SurfArgs A) {
+    int p = blockIdx.x;
+    double reach = A.R[p] + A.reach_extra;
+    int x0 = (int)ceil(A.X[3 * p] - reach), x1 = (int)floor(A.X[3 * p] + reach);
+    int y0 = (int)ceil(A.X[3 * p + 1] - reach), y1 = (int)floor(A.X[3 * p + 1] + reach);
+    int z0 = (int)ceil(A.X[3 * p + 2] - reach), z1 = (int)floor(A.X[3 * p + 2] + reach);
+    int ey = y1 - y0 + 1, ez = z1 - z0 + 1;
+    long long vol = (long long)(x1 - x0 + 1) * ey * ez;
+    uint32_t c = 0;
+    for (long long t = threadIdx.x; t < vol; t += blockDim.x) {
+        uint32_t ci, co;
+        if (surf_node(A, p, t, x0, y0, z0, ey, ez, ci, co)) ++c;
+    }
+    __shared__ uint32_t sh[32];
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+        A.count[p] = (s + 31u) & ~31u;  // padded to whole warps
+    }
+}
+
+__global__ void k_surf_fill(SurfArgs A) {
+    int p = blockIdx.x;
+    double reach = A.R[p] + A.reach_extra;
+    int x0 = (int)ceil(A.X[3 * p] - reach), x1 = (int)floor(A.X[3 * p] + reach);
+    int y0 = (int)ceil(A.X[3 * p + 1] - reach), y1 = (int)floor(A.X[3 * p + 1] + reach);
+    int z0 = (int)ceil(A.X[3 * p + 2] - reach), z1 = (int)floor(A.X[3 * p + 2] + reach);
+    int ey = y1 - y0 + 1, ez = z1 - z0 + 1;
+    long long vol = (long long)(x1 - x0 + 1) * ey * ez;
+    uint32_t base = A.offset[p];
+    uint32_t end = base + A.count[p];
+    __shared__ uint32_t sh[33];
+    __shared__ uint32_t run;
+    if (threadIdx.x == 0) run = 0;
+    __syncthreads();
+    // deterministic order: chunks of blockDim nodes, block prefix sum per chunk
+    for (long long t0 = 0; t0 < vol; t0 += blockDim.x) {
+        long long t = t0 + threadIdx.x;
+        uint32_t ci = 0, co = 0;
+        bool ok = t < vol && surf_node(A, p, t, x0, y0, z0, ey, ez, ci, co);
+        unsigned bal = __ballot_sync(0xffffffffu, ok);
+        uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        uint32_t before = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) sh[wid] = __popc(bal);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t s = 0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+                uint32_t c = sh[k];
+                sh[k] = s;
+                s += c;
+            }
+            sh[32] = s;
+        }
+        __syncthreads();
+        if (ok) {
+            uint32_t pos = base + run + sh[wid] + before;
+            A.ent[pos] = make_uint2(ci, co);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) run += sh[32];
+        __syncthreads();
+    }
+    // pad to the warp boundary and tag the warps with their sphere
+    for (uint32_t k = base + run + threadIdx.x; k < end; k += blockDim.x) A.ent[k] = make_uint2(NONE, 0u);
+    for (uint32_t k = base / 32 + threadIdx.x; k < end / 32; k += blockDim.x) A.warp_part[k] = p;
+}
+
+void launch_paint(const PaintArgs& A, int n, cudaStream_t s) {
+    if (n > 0) k_paint<<<n, 256, 0, s>>>(A);
+}
+
+void launch_words(const LayoutArgs& A, cudaStream_t s) {
+    size_t W = (size_t)A.nx * A.ny * A.nw;
+    k_words<<<(unsigned)((W + 255) / 256), 256, 0, s>>>(A);
+}
+
+void launch_words_bases(const LayoutArgs& A, uint32_t nA, cudaStream_t s) {
+    size_t W = (size_t)A.nx * A.ny * A.nw;
+    k_words_bases<<<(unsigned)((W + 255) / 256), 256, 0, s>>>(A, nA);
+}
+
+void launch_coords(const LayoutArgs& A, uint32_t nA, uint32_t nSpad, uint32_t* fbits, cudaStream_t s) {
+    size_t W = (size_t)A.nx * A.ny * A.nw;
+    k_coords<<<(unsigned)((W + 255) / 256), 256, 0, s>>>(A);
+    uint32_t nwords = nSpad / 32;
+    k_fbits<<<(nwords + 255) / 256, 256, 0, s>>>(fbits, nA, nwords);
+}
+
+void launch_gather_old(const Lat& Lnew, const Lat& Lold, cudaStream_t s) {
+    if (Lnew.nA) k_gather_old<<<(Lnew.nA + 255) / 256, 256, 0, s>>>(Lnew, Lold);
+}
+
+void launch_band_collect(const LayoutArgs& A, uint32_t* band_coord, uint32_t* count, uint32_t cap,
+                         cudaStream_t s) {
+    size_t N = (size_t)A.nx * A.ny * A.nz;
+    k_band_collect<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(A, band_coord, count, cap);
+}
+
+void launch_surf_count(const SurfArgs& A, int n, cudaStream_t s) {
+    if (n > 0) k_surf_count<<<n, 256, 0, s>>>(A);
+}
+
+void launch_surf_fill(const SurfArgs& A, int n, cudaStream_t s) {
+    if (n > 0) k_surf_fill<<<n, 256, 0, s>>>(A);
+}
+
+}  // namespace lbmdem
