@@ -34,7 +34,7 @@
  * density rho_w = rho_f; conversion signs (particle gains the momentum of a
  * covered node, loses rho_bar * V_b for an uncovered node); boundary planes
  * x = 0 and x = nx-1 are never solid; owner of a node covered by several
- * spheres = lowest particle index; populations arriving from outside the x
+ * spheres = smallest |x - X|^2 / R^2 (lowest index on a tie); populations arriving from outside the x
  * range start as the node's own reversed post-collision value (a resting
  * wall) before the inlet/outlet overwrite them; zero-gradient outlet copies
  * the unknown populations from the upstream node when that node is fluid.
@@ -90,8 +90,9 @@ struct orc_sim {
     int px; /* x periodic */
     double* f;
     double* fn;
-    int* owner; /* -1 fluid, else lowest covering particle index */
+    int* owner; /* -1 fluid, else the covering sphere of smallest |x - X|^2 / R^2 */
     int* owner_new;
+    double* best; /* that ratio, per node, while painting */
     /* particles */
     int np;
     double *X, *V, *W, *q, *R, *m, *I;
@@ -414,10 +415,14 @@ static void dem_substeps(orc_sim* s) {
 /* ------------------------------------------------------------ solid map */
 
 /* Section 2.3: a node is solid when it lies strictly inside a sphere
- * (|x - X_p|^2 < R^2, any periodic image); owner = lowest index; the inlet
- * and outlet planes stay fluid when x is not periodic. */
+ * (|x - X_p|^2 < R^2, any periodic image); the inlet and outlet planes stay
+ * fluid when x is not periodic.  A node inside several (touching) spheres
+ * belongs to the one with the smallest |x - X_p|^2 / R_p^2, the lowest index
+ * on an exact tie: each sphere then owns its own side of the contact lens,
+ * and with it the fluid links around its side of the neck. */
 static void paint(const orc_sim* s, int* owner) {
     int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
+    double* best = s->best;
     for (long n = 0; n < s->N; ++n) owner[n] = -1;
     for (int p = 0; p < s->np; ++p) {
         double cx = s->X[3 * p], cy = s->X[3 * p + 1], cz = s->X[3 * p + 2], R = s->R[p];
@@ -437,9 +442,14 @@ static void paint(const orc_sim* s, int* owner) {
                 for (int zi = z0; zi <= z1; ++zi) {
                     int z = wrapi(zi, nz);
                     double dx = xi - cx, dy = yi - cy, dz = zi - cz;
-                    if (dx * dx + dy * dy + dz * dz < R * R) {
+                    double d2 = dx * dx + dy * dy + dz * dz;
+                    if (d2 < R * R) {
                         long n = nidx(s, x, y, z);
-                        if (owner[n] < 0) owner[n] = p;
+                        double ratio = d2 / (R * R);
+                        if (owner[n] < 0 || ratio < best[n] || (ratio == best[n] && p < owner[n])) {
+                            owner[n] = p;
+                            best[n] = ratio;
+                        }
                     }
                 }
             }
@@ -641,7 +651,8 @@ orc_sim* orc_create(const orc_params* p) {
     s->fn = (double*)malloc(sizeof(double) * Q * s->N);
     s->owner = (int*)malloc(sizeof(int) * s->N);
     s->owner_new = (int*)malloc(sizeof(int) * s->N);
-    if (!s->f || !s->fn || !s->owner || !s->owner_new) {
+    s->best = (double*)malloc(sizeof(double) * s->N);
+    if (!s->f || !s->fn || !s->owner || !s->owner_new || !s->best) {
         orc_destroy(s);
         return NULL;
     }
@@ -821,6 +832,7 @@ void orc_destroy(orc_sim* s) {
     free(s->fn);
     free(s->owner);
     free(s->owner_new);
+    free(s->best);
     free(s->X);
     free(s->V);
     free(s->W);

@@ -219,3 +219,23 @@ def test_probe_matches_fields():
     expect = rho[37][sol[37] == 0].mean()
     s.step(1)
     assert abs(s.probe()[-1] - expect) < 1e-15
+
+
+def test_touching_spheres_share_the_contact_lens_symmetrically():
+    """Two equal fixed spheres overlapping by 0.1, mirror-symmetric about the
+    plane x = 14.5: each owns its own half of the contact lens (smallest
+    |x - X|^2 / R^2), and in a fluid at rest the static exchange forces of
+    Eq. 15 are mirror images that push the spheres toward each other (the
+    pressure acts on the wetted surface only)."""
+    X = np.array([[10.55, 8.3, 8.2], [18.45, 8.3, 8.2]])
+    w = workloads.Workload(name="lens", nx=29, ny=17, nz=17, tau=0.8, inlet=workloads.X_PERIODIC,
+                           X=X, R=np.array([4.0, 4.0]), fixed=np.ones(2, np.uint8), dem_substeps=1)
+    s = oracle.Oracle(w)
+    own = s.owner()
+    # the lens is split by the mid-plane
+    assert (own[:15] == 1).sum() == 0 and (own[15:] == 0).sum() == 0
+    s.step(1)
+    F = s.particles()["Fh"]
+    assert abs(F[0, 0] + F[1, 0]) < 1e-12
+    assert abs(F[0, 1] - F[1, 1]) < 1e-12 and abs(F[0, 2] - F[1, 2]) < 1e-12
+    assert F[0, 0] > 0.1
