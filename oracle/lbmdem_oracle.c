@@ -16,7 +16,14 @@
  *   2. BGK collision on every fluid node (Eqs. 4, 6, 7, 8);
  *   3. streaming (Eq. 5) with half-way moving-wall bounce-back on every
  *      fluid-solid link (Eq. 14) and the link force and torque (Eqs. 15,
- *      18, 19), on a second lattice (two-lattice push scheme);
+ *      18, 19), on a second lattice (two-lattice push scheme).  The link
+ *      momentum is counted about the rest state, c_d (f~_d + f_d* - 2 w_d
+ *      rho_f): the mean fluid pressure acts on the whole grain surface (the
+ *      paper's granular stress, Eq. 13, is an effective stress, and its
+ *      confining pressures of 0.1-30 MPa are set by the overlaps while the
+ *      mean lattice pressure maps to 2.25 GPa, Table 1).  A fully wetted
+ *      sphere is unaffected; on touching spheres the mean pressure would
+ *      otherwise press on the unwetted contact caps;
  *   4. the pressure inlet with the oscillating density (Section 2.4,
  *      Zou-He form for D3Q19, Eq. 25 and Table 2) and the outlet;
  *   5. K velocity-Verlet DEM substeps with Hertz normal and incremental
@@ -590,7 +597,12 @@ static void lbm_step(orc_sim* s) {
                     /* Eq. 14 with rho_w = rho_f and 2 w / c_s^2 = 6 w */
                     double back = ft - 6.0 * WT[m] * rf * cv;
                     s->fn[OPP[m] * N + n] = back;
-                    double Fl[3] = {CX[m] * (ft + back), CY[m] * (ft + back), CZ[m] * (ft + back)};
+                    /* Eq. 15 taken about the rest state: the mean pressure
+                     * rho_f c_s^2 acts on the whole grain (the granular
+                     * stress of Eq. 13 is an effective stress), so the
+                     * exchanged momentum is counted from 2 w rho_f */
+                    double q = ft + back - 2.0 * WT[m] * rf;
+                    double Fl[3] = {CX[m] * q, CY[m] * q, CZ[m] * q};
                     double t[3];
                     cross(r, Fl, t);
                     for (int a = 0; a < 3; ++a) {

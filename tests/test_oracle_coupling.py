@@ -224,18 +224,26 @@ def test_probe_matches_fields():
 def test_touching_spheres_share_the_contact_lens_symmetrically():
     """Two equal fixed spheres overlapping by 0.1, mirror-symmetric about the
     plane x = 14.5: each owns its own half of the contact lens (smallest
-    |x - X|^2 / R^2), and in a fluid at rest the static exchange forces of
-    Eq. 15 are mirror images that push the spheres toward each other (the
-    pressure acts on the wetted surface only)."""
+    |x - X|^2 / R^2).  Eq. 15 is counted about the rest state, so in a fluid
+    at rest at rho_f the spheres feel no force at all, while at a uniform
+    density rho_f + 0.2 the excess pressure presses on the wetted surfaces
+    only and pushes the spheres together with mirror-image forces that scale
+    with the excess (the same pair at rho_f + 0.4 feels twice the force)."""
     X = np.array([[10.55, 8.3, 8.2], [18.45, 8.3, 8.2]])
-    w = workloads.Workload(name="lens", nx=29, ny=17, nz=17, tau=0.8, inlet=workloads.X_PERIODIC,
-                           X=X, R=np.array([4.0, 4.0]), fixed=np.ones(2, np.uint8), dem_substeps=1)
-    s = oracle.Oracle(w)
-    own = s.owner()
-    # the lens is split by the mid-plane
-    assert (own[:15] == 1).sum() == 0 and (own[15:] == 0).sum() == 0
-    s.step(1)
-    F = s.particles()["Fh"]
-    assert abs(F[0, 0] + F[1, 0]) < 1e-12
-    assert abs(F[0, 1] - F[1, 1]) < 1e-12 and abs(F[0, 2] - F[1, 2]) < 1e-12
-    assert F[0, 0] > 0.1
+
+    def force(excess):
+        w = workloads.Workload(name="lens", nx=29, ny=17, nz=17, tau=0.8, inlet=workloads.X_PERIODIC,
+                               X=X, R=np.array([4.0, 4.0]), fixed=np.ones(2, np.uint8), dem_substeps=1)
+        s = oracle.Oracle(w)
+        own = s.owner()
+        assert (own[:15] == 1).sum() == 0 and (own[15:] == 0).sum() == 0
+        s.set_populations(s.populations() * (1.0 + excess))
+        s.step(1)
+        return s.particles()["Fh"]
+
+    assert np.abs(force(0.0)).max() < 1e-12
+    F1, F2 = force(0.2), force(0.4)
+    assert abs(F1[0, 0] + F1[1, 0]) < 1e-12
+    assert abs(F1[0, 1] - F1[1, 1]) < 1e-12 and abs(F1[0, 2] - F1[1, 2]) < 1e-12
+    assert F1[0, 0] > 0.1
+    assert abs(F2[0, 0] - 2 * F1[0, 0]) < 1e-9 * F1[0, 0]
