@@ -1,0 +1,361 @@
+"""Benchmark of the coupled LBM-DEM step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: the 128 x 128 x 1024 column (x = 1024, propagation axis) with 2048
+spheres R = 11.4 on an FCC lattice a = 32 (4 x 4 x 32 cells), tau 0.6,
+sinusoidal inlet (amplitude 1e-3, period 400), seeded jitter 1e-3 R, FP32
+populations; synthetic input from workloads.config_scale().
+
+metric: coupled-step MLUPS over fluid nodes (fluid-node updates per second,
+millions), whole job.  The `roofline` object is for the dominant kernel,
+collide+stream (both AA parities), at 152 algorithmic bytes per fluid node
+(19 FP32 populations read and written), its duration taken with CUDA events
+around every launch inside the timed region.  `e2e` times the same workload
+through the C ABI from host buffers: set_packing (host -> device), the K
+steps, and the read-back of the sphere state and the probe trace
+(device -> host).  `cpu_baseline` times the FP64 oracle on a few steps of the
+same workload on the host cores.  Multi-GPU (torchrun): every rank runs its
+own column (independent problems, no collective), value = all ranks' fluid
+updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_FLUID_NODE = 152  # 19 populations x 4 B, read + write
+METRIC = "coupled step MLUPS (fluid nodes)"
+UNIT = "MLUPS"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("lattice.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1808_08921_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per collide+stream launch from the committed ncu summary, if
+    it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "coupled_step_fcc128x128x1024.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    kh = None
+    val = None
+    for line in txt.splitlines():
+        if line.startswith("kernel_source_hash:"):
+            kh = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch_full_size:"):
+            try:
+                val = float(line.split(":", 1)[1].strip())
+            except ValueError:
+                val = None
+    return val if kh == _kernel_hash() else None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_1808_08921_gb300 import lbmdem
+
+    rank, world, local = _dist()
+    dev = local
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    w = workloads.config_scale(steps=args.steps)
+    stream = torch.cuda.current_stream()
+    over = dict(device=dev, cuda_stream=stream.cuda_stream, skin=0.25, dem_skin=0.5)
+    sim = lbmdem.Sim.from_workload(w, **over)
+    cnt0 = sim.counters()
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    sim.set_timing(True)
+    cnt_a = sim.counters()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with Clocks(dev) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    tm = sim.timing()
+    cnt_b = sim.counters()
+    sim.set_timing(False)
+    st = sim.status()
+    fluid = cnt_b["fluid"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, float(fluid)], device="cuda", dtype=torch.float64)
+        ts = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(ts, t)
+        ms_max = max(float(x[0]) for x in ts)
+        fluid_sum = sum(float(x[1]) for x in ts)
+    else:
+        ms_max, fluid_sum = ms, float(fluid)
+    value = fluid_sum * args.steps / (ms_max * 1e-3) / 1e6
+    # roofline of the dominant kernel (collide+stream, both parities)
+    k1_ms, k1_n = tm["collide_stream"]
+    k1_avg = k1_ms / max(k1_n, 1)
+    peak, peak_kind = _peaks()
+    achieved = BYTES_PER_FLUID_NODE * fluid / (k1_avg * 1e-3) / 1e9
+    traffic = _profiled_traffic()
+    # end to end through the C ABI from host buffers
+    e2e = None
+    if not args.no_e2e:
+        sim2 = lbmdem.Sim(lbmdem.params_from_workload(w, **over))
+        sim2.set_pressure_source(w.waveform, w.amplitude, w.omega, w.t_n, w.t0)
+        n = w.n_particles
+        h2d = 8 * (3 * n + n + 3 * n + 3 * n) + n  # X, R, V, Omega (FP64) + fixed flags
+        d2h = 8 * 19 * n  # X, V, Omega, q, F, T (FP64)
+        barrier()
+        t0 = time.perf_counter()
+        sim2.set_packing(w.X, w.R, np.zeros((n, 3)), np.zeros((n, 3)), w.fixed)
+        sim2.step(args.steps)
+        P = sim2.particles()
+        barrier()
+        t1 = time.perf_counter()
+        fl2 = sim2.counters()["fluid"]
+        e2e = {"value": round(fl2 * args.steps / (t1 - t0) / 1e6, 1), "unit": UNIT,
+               "h2d_bytes_per_step": round(h2d / args.steps, 1),
+               "d2h_bytes_per_step": round(d2h / args.steps, 1),
+               "includes": "set_packing (layout build) + steps + read_particles"}
+        sim2.close()
+    launches = cnt_b["launches"] - cnt_a["launches"]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        groups = {k: {"ms_total": round(v[0], 3), "launches": v[1],
+                      "us_avg": round(1e3 * v[0] / max(v[1], 1), 2)} for k, v in tm.items()}
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "lattice": [w.nx, w.ny, w.nz], "spheres": w.n_particles,
+                       "fluid_nodes": fluid, "stored_nodes": cnt_b["stored"], "tau": w.tau,
+                       "dem_substeps": w.dem_substeps, "source": "sine amplitude 1e-3 period 400",
+                       "mlups_all_nodes": round(value * cnt_b["nodes"] / max(fluid, 1), 1),
+                       "l2": "inputs larger than L2: populations %.0f MB" % (19 * 4 * cnt_b["stored"] / 1e6),
+                       "relayouts_in_timed_region": cnt_b["relayouts"] - cnt_a["relayouts"],
+                       "status": st},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "kernel": "collide_stream (even+odd AA)", "peak_kind": peak_kind,
+                         "bytes_per_launch": BYTES_PER_FLUID_NODE * fluid,
+                         "us_per_launch": round(1e3 * k1_avg, 2)},
+            "kernel_groups": groups,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    sim.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _oracle_sample(steps_budget_s, max_steps=None):
+    """Time the FP64 oracle on the same 128x128x1024 column, one step at a
+    time, until the budget is spent (at least one step)."""
+    import oracle
+    import workloads
+    w = workloads.config_scale(steps=1)
+    o = oracle.Oracle(w)
+    _, _, sol = o.fields()
+    fluid = int((sol == 0).sum())
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        o.step(1)
+        times.append(time.perf_counter() - t0)
+        if max_steps and len(times) >= max_steps:
+            break
+        if not max_steps and time.perf_counter() - t_start > steps_budget_s:
+            break
+    o.close()
+    return fluid, times
+
+
+def cpu_baseline(budget_s):
+    fluid, times = _oracle_sample(budget_s)
+    mlups = fluid * len(times) / sum(times) / 1e6
+    return {"value": round(mlups, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} coupled steps of the 128x128x1024 column (2048 spheres), "
+                      f"FP64 single-threaded C, {sum(times):.1f} s"}
+
+
+def _slab(cells_x):
+    """x-slab of the same FCC column: 128 x 128 cross-section, 32 * cells_x
+    lattice units long, same sphere size, spacing, tau and source."""
+    import workloads
+    return workloads.fcc_column(32 * cells_x, 128, 128, 0.6, 32.0, 11.4, jitter=1e-3 * 11.4,
+                                seed=2, period=400, mu=0.3, substeps=10, steps=1,
+                                name=f"fcc128x128x{32 * cells_x}_a32_R11.4_tau0.6")
+
+
+def run_reference(args):
+    """The FP64 oracle timed on the host cores on the same workload.  Each
+    step is one coupled oracle step on an x-slab of the column (same cross-
+    section and packing), the slab sized so that the whole run fits in about
+    args.ref_seconds; MLUPS over fluid nodes is comparable across lengths."""
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    w1 = _slab(1)
+    o = oracle.Oracle(w1)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    o.close()
+    per_step = args.ref_seconds / max(args.steps + args.warmup, 1)
+    cells = int(max(1, min(32, per_step / max(t1, 1e-6))))
+    w = _slab(cells)
+    o = oracle.Oracle(w)
+    _, _, sol = o.fields()
+    fluid = int((sol == 0).sum())
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    o.close()
+    value = fluid * args.steps / dt / 1e6
+    sample = (f"{args.steps} timed coupled steps (+{args.warmup} warm-up) of a "
+              f"{w.nx}-long x-slab of the 128x128x1024 column ({w.n_particles} spheres), "
+              f"FP64 single-threaded C")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * dt / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fcc128x128x1024_a32_R11.4_tau0.6", "sample_lattice": [w.nx, w.ny, w.nz],
+                       "sample_spheres": w.n_particles, "sample_fluid_nodes": fluid},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        args.steps = 20 if args.steps is None else args.steps
+        args.warmup = 3 if args.warmup is None else args.warmup
+        run_reference(args)
+        return
+    args.steps = 2000 if args.steps is None else args.steps
+    args.warmup = 200 if args.warmup is None else args.warmup
+    if args.warmup < 3:
+        args.warmup = 3
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -165,8 +165,9 @@ int lbm_dem_read_monitors(lbmdem_ctx* c, double out[6]);
 /* Counters of the current layout: out[0] lattice nodes, [1] stored nodes,
  * [2] fluid nodes now, [3] surface nodes tracked for conversion, [4] link
  * candidate nodes, [5] neighbour-list entries, [6] time step t, [7]
- * re-layouts done, [8] node conversions so far.  Synchronises. */
-int lbm_dem_read_counters(lbmdem_ctx* c, int64_t out[9]);
+ * re-layouts done, [8] node conversions so far, [9] kernels launched by
+ * lbm_dem_step so far.  Synchronises. */
+int lbm_dem_read_counters(lbmdem_ctx* c, int64_t out[10]);
 
 /* Per-kernel timing with CUDA events on the context stream.  enable = 1
  * brackets every launch group of the following steps with event pairs;

@@ -79,6 +79,7 @@ struct lbmdem_ctx {
     double skin = 0.25, dem_skin = 0.5, trigger = 0.0, hard = 0.0;
     // lattice
     DBuf<int32_t> owner;
+    DBuf<unsigned long long> paint_best;
     DBuf<uint8_t> deep, band;
     DBuf<uint4> rec, rec2;
     DBuf<uint32_t> maskB, maskB2, cntA, cntB, scan_tmp;
@@ -134,6 +135,9 @@ struct lbmdem_ctx {
     bool gtiming = false;
     int64_t relayouts = 0;
     int64_t steps_until_check = 0;
+    bool capturing = false;      // inside stream capture (events become graph nodes)
+    int64_t launches = 0;        // kernels enqueued by the step loop
+    int64_t glaunches = 0;       // kernels in one captured graph
 };
 
 // ------------------------------------------------------------ helpers
@@ -359,10 +363,15 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
     if (fresh) fill_i32(c->owner.p, OWNER_FLUID, c->N, s);
     CK(cudaMemsetAsync(c->deep.p, 0, c->N, s));
     CK(cudaMemsetAsync(c->band.p, 0, c->N, s));
-    PaintArgs PA{c->Xref.p, c->Rd.p, nx, ny, nz, px, c->skin, fresh ? c->owner.p : nullptr, c->deep.p,
-                 c->band.p};
-    launch_paint(PA, c->np, s);
+    if (fresh) CK(c->paint_best.alloc(c->N));
+    PaintArgs PA{c->Xref.p, c->Rd.p, nx, ny, nz, px, c->skin, fresh ? c->owner.p : nullptr,
+                 fresh ? c->paint_best.p : nullptr, c->deep.p, c->band.p};
+    launch_paint(PA, c->np, c->N, s);
     CK(cudaGetLastError());
+    if (fresh) {
+        CK(cudaStreamSynchronize(s));
+        c->paint_best.release();
+    }
     // words into the spare record set (the current one is needed for the copy)
     LayoutArgs LA{nx, ny, nz, c->nw, c->owner.p, c->deep.p, c->band.p, c->rec2.p, c->maskB2.p,
                   c->cntA.p, c->cntB.p, nullptr};
@@ -488,15 +497,38 @@ static void record_pair_begin(lbmdem_ctx* c, int group, size_t& idx) {
     }
     if (c->ev_group.size() < c->ev_pairs) c->ev_group.resize(c->ev_pairs);
     c->ev_group[idx] = group;
-    cudaEventRecord(c->ev[2 * idx], c->stream);
+    if (c->capturing)
+        cudaEventRecordWithFlags(c->ev[2 * idx], c->stream, cudaEventRecordExternal);
+    else
+        cudaEventRecord(c->ev[2 * idx], c->stream);
 }
 
-static void record_pair_end(lbmdem_ctx* c, size_t idx) { cudaEventRecord(c->ev[2 * idx + 1], c->stream); }
+static void record_pair_end(lbmdem_ctx* c, size_t idx) {
+    if (c->capturing)
+        cudaEventRecordWithFlags(c->ev[2 * idx + 1], c->stream, cudaEventRecordExternal);
+    else
+        cudaEventRecord(c->ev[2 * idx + 1], c->stream);
+}
+
+// kernels one step issues: map update (4 when there is a band, else 1),
+// collide, links (if any surface entries), inlet/outlet (if any), DEM
+static int64_t kernels_per_step(const lbmdem_ctx* c) {
+    int64_t k = 1;  // DEM
+    if (c->lbm) {
+        k += c->nband ? 4 : 1;
+        k += c->nS ? 1 : 0;
+        k += c->nwarps ? 1 : 0;
+        bool px = c->p.inlet == LBMDEM_X_PERIODIC;
+        k += (!px && !(c->p.inlet != 0 && c->p.outlet > 1)) ? 1 : 0;
+    }
+    return k;
+}
 
 static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
     cudaStream_t s = c->stream;
     bool tm = c->timing;
     size_t e = 0;
+    c->launches += kernels_per_step(c);
     if (c->lbm) {
         Lat L = make_lat(c);
         PartView P = make_part(c);
@@ -572,8 +604,11 @@ static int capture_graph(lbmdem_ctx* c) {
     destroy_graph(c);
     if (int r = collect_timing(c)) return r;
     bool mon = c->p.monitor_every > 0;
+    int64_t l0 = c->launches;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
     for (int k = 0; k < c->glen; ++k) enqueue_step(c, k & 1, mon && k == c->glen - 1);
+    c->capturing = false;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess) return fail(c, LBMDEM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
@@ -583,6 +618,8 @@ static int capture_graph(lbmdem_ctx* c) {
     c->gtiming = c->timing;
     // event pairs recorded during capture belong to the graph: they are
     // recorded again by every launch and read back after it
+    c->glaunches = c->launches - l0;
+    c->launches = l0;  // counted when the graph is launched
     c->gpairs = c->ev_pairs;
     c->gev_group.assign(c->ev_group.begin(), c->ev_group.begin() + c->gpairs);
     c->ev_pairs = 0;
@@ -610,10 +647,12 @@ static int check_and_relayout(lbmdem_ctx* c, bool& did) {
         did = true;
         disp = 0.f;
     }
+    // next check: before the fastest sphere could reach the trigger at twice
+    // its current speed, and at least every 64 steps (spheres accelerate)
     double room = c->trigger - disp;
     double v = std::max<double>(vel, 1e-9);
     double steps = room > 0 ? room / (2.0 * v) : 1.0;
-    c->steps_until_check = (int64_t)std::max(1.0, std::min(steps, 1.0e9));
+    c->steps_until_check = (int64_t)std::max(1.0, std::min(steps, 64.0));
     return 0;
 }
 
@@ -913,6 +952,7 @@ int lbm_dem_step(lbmdem_ctx* c, int64_t n) {
                 if (int r = capture_graph(c)) return r;
             }
             CK(cudaGraphLaunch(c->gexec, c->stream));
+            c->launches += c->glaunches;
             if (c->p.monitor_every > 0) c->mon_step = c->t + c->glen - 1;
             c->t += c->glen;
             n -= c->glen;
@@ -1075,7 +1115,7 @@ int lbm_dem_read_monitors(lbmdem_ctx* c, double out[6]) {
     return lbm_dem_status(c);
 }
 
-int lbm_dem_read_counters(lbmdem_ctx* c, int64_t out[9]) {
+int lbm_dem_read_counters(lbmdem_ctx* c, int64_t out[10]) {
     if (!c || !out) return LBMDEM_ERR_INVALID_ARG;
     CK(cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -1102,6 +1142,7 @@ int lbm_dem_read_counters(lbmdem_ctx* c, int64_t out[9]) {
     out[6] = c->t;
     out[7] = c->relayouts;
     out[8] = (int64_t)c->st_host->flips_total;
+    out[9] = c->launches;
     return 0;
 }
 

@@ -65,12 +65,6 @@ __host__ __device__ constexpr float wt(int m) {
            : (cx(m) * cx(m) + cy(m) * cy(m) + cz(m) * cz(m)) == 1 ? 1.0f / 18.0f
                                                                   : 1.0f / 36.0f;
 }
-// 36 * w as an integer (12, 2, 1) for exact static-pressure sums.
-__host__ __device__ constexpr int wt36(int m) {
-    return (cx(m) * cx(m) + cy(m) * cy(m) + cz(m) * cz(m)) == 0 ? 12
-           : (cx(m) * cx(m) + cy(m) * cy(m) + cz(m) * cz(m)) == 1 ? 2
-                                                                  : 1;
-}
 // Opposite direction: the pairs of Eq. 3 are (0,1) (2,3) (4,5) (6,11) (7,10)
 // (8,13) (9,12) (14,17) (15,16) and 18 alone.
 __host__ __device__ constexpr int opp(int m) {
@@ -186,6 +180,13 @@ struct PartView {
 __device__ __forceinline__ bool inside_exact(double ax, double ay, double az, double R) {
     double s = __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az));
     return s < __dmul_rn(R, R);
+}
+
+// |y - X|^2 / R^2 with the same operation order and rounding as the test
+// above; among the spheres that contain a node, the smallest ratio owns it.
+__device__ __forceinline__ double inside_ratio(double ax, double ay, double az, double R) {
+    double s = __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az));
+    return __ddiv_rn(s, __dmul_rn(R, R));
 }
 
 __device__ __forceinline__ double minimg(double d, double L, int periodic) {

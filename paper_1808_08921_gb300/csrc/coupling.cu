@@ -6,13 +6,15 @@
 //    post-collision value f~_d(x) (AA layout, either parity); it is replaced
 //    by the bounced value f~_d - 6 w_d rho_f c_d . V_b (Eq. 14, moving wall
 //    with V_b = V + Omega x (x_b - X), x_b = x + c_d / 2), and the link force
-//    c_d (f~_d + f_bounced) (Eq. 15) and its torque (Eq. 19) are summed by
-//    warp shuffles, then one FP64 atomic per warp per component.  The
-//    static part 2 w_d rho_f c_d of each link force is summed exactly in
-//    integers (36 w_d is 2 or 1).
+//    c_d (f~_d + f_bounced - 2 w_d rho_f) (Eq. 15, counted about the rest
+//    state: the mean pressure acts on the whole grain, and with populations
+//    stored as deviations from w_d rho_f this is c_d (2 g~_d - delta)) and
+//    its torque (Eq. 19) are summed by warp shuffles, then one FP64 atomic
+//    per warp per component.
 //  * map update: every node within `skin` of a sphere surface is re-tested
-//    against the current sphere positions (lowest index wins where spheres
-//    overlap; the inlet/outlet planes stay fluid).  Changed nodes are
+//    against the current sphere positions (where spheres overlap, the one
+//    with the smallest |x - X|^2 / R^2 owns the node, the lowest index on a
+//    tie; the inlet/outlet planes stay fluid).  Changed nodes are
 //    queued; for each, the natural populations of the node and its 18
 //    neighbours are gathered with the old map, the conversion is applied
 //    (covered node: its momentum goes to the sphere, Eq. 16; uncovered node:
@@ -41,7 +43,6 @@ __global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
     int p = B.warp_part[w];
     uint2 ent = B.ent[e];
     float Fx = 0.f, Fy = 0.f, Fz = 0.f, Tx = 0.f, Ty = 0.f, Tz = 0.f;
-    int S1x = 0, S1y = 0, S1z = 0, S2x = 0, S2y = 0, S2z = 0;
     float4 xf = P.xf[p];
     if (ent.x != NONE && fluid_bit(L, ent.x)) {
         int x, y, z;
@@ -81,13 +82,6 @@ __global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
             Tx += ry * qz - rz * qy;
             Ty += rz * qx - rx * qz;
             Tz += rx * qy - ry * qx;
-            const int w36 = wt36(m);
-            S1x += w36 * cx(m);
-            S1y += w36 * cy(m);
-            S1z += w36 * cz(m);
-            S2x += w36 * (iy * cz(m) - iz * cy(m));
-            S2y += w36 * (iz * cx(m) - ix * cz(m));
-            S2z += w36 * (ix * cy(m) - iy * cx(m));
         }
     }
     const unsigned full = 0xffffffffu;
@@ -99,29 +93,16 @@ __global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
         Tx += __shfl_xor_sync(full, Tx, o);
         Ty += __shfl_xor_sync(full, Ty, o);
         Tz += __shfl_xor_sync(full, Tz, o);
-        S1x += __shfl_xor_sync(full, S1x, o);
-        S1y += __shfl_xor_sync(full, S1y, o);
-        S1z += __shfl_xor_sync(full, S1z, o);
-        S2x += __shfl_xor_sync(full, S2x, o);
-        S2y += __shfl_xor_sync(full, S2y, o);
-        S2z += __shfl_xor_sync(full, S2z, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        // static part: 2 rho_f w_d c_d summed exactly, torque lever r = i - xf
-        double k = 2.0 * (double)L.rho_f / 36.0;
-        double s1[3] = {(double)S1x, (double)S1y, (double)S1z};
-        double xfx = xf.x, xfy = xf.y, xfz = xf.z;
-        double tsx = (double)S2x - (xfy * s1[2] - xfz * s1[1]);
-        double tsy = (double)S2y - (xfz * s1[0] - xfx * s1[2]);
-        double tsz = (double)S2z - (xfx * s1[1] - xfy * s1[0]);
         double* F = P.Fh + 3 * p;
         double* T = P.Th + 3 * p;
-        atomicAdd(F + 0, (double)Fx + k * s1[0]);
-        atomicAdd(F + 1, (double)Fy + k * s1[1]);
-        atomicAdd(F + 2, (double)Fz + k * s1[2]);
-        atomicAdd(T + 0, (double)Tx + k * tsx);
-        atomicAdd(T + 1, (double)Ty + k * tsy);
-        atomicAdd(T + 2, (double)Tz + k * tsz);
+        atomicAdd(F + 0, (double)Fx);
+        atomicAdd(F + 1, (double)Fy);
+        atomicAdd(F + 2, (double)Fz);
+        atomicAdd(T + 0, (double)Tx);
+        atomicAdd(T + 1, (double)Ty);
+        atomicAdd(T + 2, (double)Tz);
     }
 }
 
@@ -174,8 +155,9 @@ __global__ void k_map_band(MapArgs A) {
     int4 cand = A.band.cand[k];
     int c4[4] = {cand.x, cand.y, cand.z, cand.w};
     int best = OWNER_FLUID;
+    double best_ratio = 0.0;
     if (L.px || (x > 0 && x < L.nx - 1)) {
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < 4; ++a) {  // candidates ascend, so ties keep the lowest index
             int p = c4[a];
             if (p < 0) break;
             double X0, X1, X2;
@@ -183,9 +165,13 @@ __global__ void k_map_band(MapArgs A) {
             double ax = node_offset(x, X0, L.nx, L.px);
             double ay = node_offset(y, X1, L.ny, 1);
             double az = node_offset(z, X2, L.nz, 1);
-            if (inside_exact(ax, ay, az, A.P.Rd[p])) {
-                best = p;
-                break;
+            double Rp = A.P.Rd[p];
+            if (inside_exact(ax, ay, az, Rp)) {
+                double r = inside_ratio(ax, ay, az, Rp);
+                if (best == OWNER_FLUID || r < best_ratio) {
+                    best = p;
+                    best_ratio = r;
+                }
             }
         }
     }

@@ -4,7 +4,9 @@
 // good part of the skin since the last one).  Steps:
 //   1. paint: for every sphere, every node of its bounding box (all periodic
 //      images) is tested with the exact FP64 rule |y - X|^2 < R^2 shared with
-//      the map update; the owner is the lowest covering index (atomicMin).
+//      the map update; a node inside several spheres belongs to the one with
+//      the smallest |y - X|^2 / R^2 (first pass: atomicMin of the FP64 ratio
+//      bits; second pass: lowest index among the equal ratios).
 //      Only set_packing paints owners: after step t the map belongs to the
 //      positions of that step's map update, one DEM update behind the
 //      current ones, so a re-layout keeps the maintained map (the next map
@@ -97,6 +99,7 @@ __device__ __forceinline__ int wrapi(int a, int L) {
     return r < 0 ? r + L : r;
 }
 
+template <int PASS>
 __global__ void k_paint(PaintArgs A) {
     int p = blockIdx.x;
     double X0 = A.X[3 * p], X1 = A.X[3 * p + 1], X2 = A.X[3 * p + 2];
@@ -123,7 +126,14 @@ __global__ void k_paint(PaintArgs A) {
         int y = wrapi(yi, A.ny), z = wrapi(zi, A.nz);
         double ax = (double)xi - X0, ay = (double)yi - X1, az = (double)zi - X2;
         size_t li = ((size_t)x * A.ny + y) * A.nz + z;
-        if (A.owner && inside_exact(ax, ay, az, R)) atomicMin(&A.owner[li], p);
+        if (A.owner && inside_exact(ax, ay, az, R)) {
+            unsigned long long rb = (unsigned long long)__double_as_longlong(inside_ratio(ax, ay, az, R));
+            if (PASS == 0)
+                atomicMin(&A.best[li], rb);
+            else if (A.best[li] == rb)
+                atomicMin(&A.owner[li], p);
+        }
+        if (PASS == 1) continue;
         double d2 = ax * ax + ay * ay + az * az;
         if (Rin > 0 && d2 < Rin * Rin) A.deep[li] = 1;
         if (d2 < Rout * Rout && (Rin <= 0 || d2 >= Rin * Rin)) A.band[li] = 1;
@@ -315,8 +325,16 @@ __global__ void k_surf_fill(SurfArgs A) {
     for (uint32_t k = base / 32 + threadIdx.x; k < end / 32; k += blockDim.x) A.warp_part[k] = p;
 }
 
-void launch_paint(const PaintArgs& A, int n, cudaStream_t s) {
-    if (n > 0) k_paint<<<n, 256, 0, s>>>(A);
+__global__ void k_fill_u64(unsigned long long* p, unsigned long long v, size_t n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+void launch_paint(const PaintArgs& A, int n, size_t N, cudaStream_t s) {
+    if (n <= 0) return;
+    if (A.owner) k_fill_u64<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(A.best, ~0ull, N);
+    k_paint<0><<<n, 256, 0, s>>>(A);
+    if (A.owner) k_paint<1><<<n, 256, 0, s>>>(A);
 }
 
 void launch_words(const LayoutArgs& A, cudaStream_t s) {

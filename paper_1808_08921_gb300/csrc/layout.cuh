@@ -11,6 +11,7 @@ struct PaintArgs {
     int nx, ny, nz, px;
     double skin;
     int32_t* owner;  // null: keep the current owner map (re-layout)
+    unsigned long long* best;  // per node: smallest |y - X|^2 / R^2 (FP64 bits)
     uint8_t* deep;
     uint8_t* band;
 };
@@ -81,7 +82,7 @@ struct BandCand {
 void fill_i32(int32_t* p, int32_t v, size_t n, cudaStream_t s);
 void exclusive_scan(const uint32_t* in, uint32_t* out, size_t n, uint32_t* tmp, cudaStream_t s);
 size_t scan_tmp_size(size_t n);
-void launch_paint(const PaintArgs& A, int n, cudaStream_t s);
+void launch_paint(const PaintArgs& A, int n, size_t N, cudaStream_t s);
 void launch_words(const LayoutArgs& A, cudaStream_t s);
 void launch_words_bases(const LayoutArgs& A, uint32_t nA, cudaStream_t s);
 void launch_coords(const LayoutArgs& A, uint32_t nA, uint32_t nSpad, uint32_t* fbits, cudaStream_t s);
