@@ -147,7 +147,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
     w = workloads.config_scale(steps=args.steps)
     stream = torch.cuda.current_stream()
-    over = dict(device=dev, cuda_stream=stream.cuda_stream, skin=0.25, dem_skin=0.5)
+    over = dict(device=dev, cuda_stream=stream.cuda_stream, skin=0.1, dem_skin=0.5)
     sim = lbmdem.Sim.from_workload(w, **over)
     cnt0 = sim.counters()
     sim.step(args.warmup)

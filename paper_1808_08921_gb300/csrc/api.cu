@@ -90,8 +90,8 @@ struct lbmdem_ctx {
     DBuf<int4> band_cand;
     uint32_t nband = 0;
     DBuf<uint32_t> surf_count, surf_off;
-    DBuf<uint2> surf_ent;
-    DBuf<int32_t> warp_part;
+    DBuf<uint2> surf_link;
+    DBuf<uint32_t> warp_pd;
     uint32_t nwarps = 0;
     DBuf<Flip> flip_rec;
     DBuf<float> flip_scratch;
@@ -105,7 +105,7 @@ struct lbmdem_ctx {
     DBuf<double> Xref, Fh, Th, Rd, Fh_prev, Th_prev;
     DBuf<float4> Fa, Ta;
     DBuf<float4> dX, dXc, dXb, V, Om, q, Vhb, Whb, Fc, Tc, xf;
-    DBuf<int4> org;
+    DBuf<int4> org, orgw;
     DBuf<float> R, invm, invI;
     DBuf<uint8_t> fixed;
     int nbmax = 48;
@@ -210,6 +210,7 @@ static PartView make_part(lbmdem_ctx* c) {
     P.R = c->R.p;
     P.Rd = c->Rd.p;
     P.org = c->org.p;
+    P.orgw = c->orgw.p;
     P.xf = c->xf.p;
     P.Fh = c->Fh.p;
     P.Th = c->Th.p;
@@ -253,6 +254,7 @@ static Dem make_dem(lbmdem_ctx* c) {
     D.nb_dref = c->nb_dref.p;
     D.nb_ft = c->nb_ft.p;
     D.org = c->org.p;
+    D.orgw = c->orgw.p;
     D.xf = c->xf.p;
     DevStats* s = c->st.p;
     D.status = &s->status;
@@ -431,32 +433,36 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
     CK(c->band_cand.ensure(std::max<uint32_t>(nband, 1)));
     if (int r = build_cells(c)) return r;
     BandCand BC{c->Xref.p, c->Rd.p, c->skin, c->grid, c->cell_start.p, c->cell_order.p,
-                c->band_coord.p, c->band_cand.p, nband, &c->st.p->status};
+                c->band_coord.p, c->band_cand.p, nband, &c->st.p->status, c->band.p, nx, ny, nz};
     launch_band_cand(BC, s);
     CK(cudaGetLastError());
-    // surface lists for the link kernel
+    // link lists, grouped by (sphere, direction)
     int np = c->np;
-    CK(c->surf_count.ensure(np + 1));
-    CK(c->surf_off.ensure(np + 1));
-    CK(cudaMemsetAsync(c->surf_count.p, 0, sizeof(uint32_t) * (np + 1), s));
+    size_t ng = (size_t)std::max(np, 1) * (Q - 1);
+    CK(c->surf_count.ensure(ng + 1));
+    CK(c->surf_off.ensure(ng + 1));
+    CK(cudaMemsetAsync(c->surf_count.p, 0, sizeof(uint32_t) * (ng + 1), s));
     SurfArgs SA{};
     SA.L = make_lat(c);
     SA.X = c->Xref.p;
     SA.R = c->Rd.p;
     SA.reach_extra = c->skin + 1.5;
+    SA.skin = c->skin;
+    SA.owner = c->owner.p;
+    SA.band = c->band.p;
     SA.count = c->surf_count.p;
     launch_surf_count(SA, np, s);
-    exclusive_scan(c->surf_count.p, c->surf_off.p, np + 1, c->scan_tmp.p, s);
-    uint32_t nent = 0;
-    if (int r = read_u32(c, c->surf_off.p + np, &nent)) return r;
-    CK(c->surf_ent.ensure(std::max<uint32_t>(nent, 32)));
-    CK(c->warp_part.ensure(std::max<uint32_t>(nent / 32, 1)));
+    exclusive_scan(c->surf_count.p, c->surf_off.p, ng + 1, c->scan_tmp.p, s);
+    uint32_t nlink = 0;
+    if (int r = read_u32(c, c->surf_off.p + ng, &nlink)) return r;
+    CK(c->surf_link.ensure(std::max<uint32_t>(nlink, 32)));
+    CK(c->warp_pd.ensure(std::max<uint32_t>(nlink / LINK_WARP, 1)));
     SA.offset = c->surf_off.p;
-    SA.ent = c->surf_ent.p;
-    SA.warp_part = c->warp_part.p;
+    SA.link = c->surf_link.p;
+    SA.warp_pd = c->warp_pd.p;
     launch_surf_fill(SA, np, s);
     CK(cudaGetLastError());
-    c->nwarps = nent / 32;
+    c->nwarps = nlink / LINK_WARP;
     // conversion scratch
     uint32_t cap = c->p.max_flips > 0 ? (uint32_t)c->p.max_flips
                                       : std::min<uint32_t>(1u << 20, std::max<uint32_t>(4096u, nband / 8));
@@ -555,7 +561,7 @@ static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
         if (tm) record_pair_begin(c, 0, e);
         launch_collide(L, mon, parity == 1, monitor, s);
         if (tm) record_pair_end(c, e);
-        LinkLists LL{c->surf_ent.p, c->warp_part.p, c->nwarps};
+        LinkLists LL{c->surf_link.p, c->warp_pd.p, c->nwarps};
         if (tm) record_pair_begin(c, 1, e);
         launch_links(L, P, LL, s);
         if (tm) record_pair_end(c, e);
@@ -757,7 +763,7 @@ int lbm_dem_init(const lbmdem_params* pp, lbmdem_ctx** out) {
         if (c->owner.alloc(c->N) || c->deep.alloc(c->N) || c->band.alloc(c->N) || c->rec.alloc(c->W) ||
             c->rec2.alloc(c->W) || c->maskB.alloc(c->W) || c->maskB2.alloc(c->W) ||
             c->cntA.alloc(c->W + 1) || c->cntB.alloc(c->W + 1) ||
-            c->scan_tmp.alloc(scan_tmp_size(std::max(c->W + 1, (size_t)1 << 20))) ||
+            c->scan_tmp.alloc(scan_tmp_size(std::max(c->W + 1, (size_t)1 << 24))) ||
             c->band_count.alloc(1))
             return bail(LBMDEM_ERR_OOM);
     }
@@ -790,6 +796,8 @@ int lbm_dem_set_packing(lbmdem_ctx* c, int32_t n, const double* X, const double*
     }
     // geometry limits: a node is near at most one image of a sphere, and a
     // sphere meets each image of a neighbour through one neighbour entry
+    if (c->lbm && Rmax + c->skin + 3.0 >= 127.0)
+        return fail(c, LBMDEM_ERR_INVALID_ARG, "R + skin must stay below 124 lattice units");
     double lim_lbm = Rmax + c->skin + 1.5;
     double lim_dem = 2 * Rmax + c->dem_skin;
     double Ls[3] = {(double)p.nx, (double)p.ny, (double)p.nz};
@@ -821,8 +829,8 @@ int lbm_dem_set_packing(lbmdem_ctx* c, int32_t n, const double* X, const double*
     destroy_graph(c);
     size_t nn = std::max(n, 1);
     CK(c->Xref.alloc(3 * nn));
-    CK(c->Fh.alloc(3 * nn));
-    CK(c->Th.alloc(3 * nn));
+    CK(c->Fh.alloc(3 * NREP * nn));
+    CK(c->Th.alloc(3 * NREP * nn));
     CK(c->Fh_prev.alloc(3 * nn));
     CK(c->Th_prev.alloc(3 * nn));
     CK(c->Fa.alloc(nn));
@@ -839,6 +847,7 @@ int lbm_dem_set_packing(lbmdem_ctx* c, int32_t n, const double* X, const double*
     CK(c->Tc.alloc(nn));
     CK(c->xf.alloc(nn));
     CK(c->org.alloc(nn));
+    CK(c->orgw.alloc(nn));
     CK(c->R.alloc(nn));
     CK(c->Rd.alloc(nn));
     CK(c->invm.alloc(nn));
@@ -885,8 +894,8 @@ int lbm_dem_set_packing(lbmdem_ctx* c, int32_t n, const double* X, const double*
     CK(cudaMemcpyAsync(c->invm.p, imv.data(), sizeof(float) * nn, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->invI.p, iIv.data(), sizeof(float) * nn, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->fixed.p, fx.data(), nn, cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(c->Fh.p, 0, sizeof(double) * 3 * nn, s));
-    CK(cudaMemsetAsync(c->Th.p, 0, sizeof(double) * 3 * nn, s));
+    CK(cudaMemsetAsync(c->Fh.p, 0, sizeof(double) * 3 * NREP * nn, s));
+    CK(cudaMemsetAsync(c->Th.p, 0, sizeof(double) * 3 * NREP * nn, s));
     CK(cudaMemsetAsync(c->Fh_prev.p, 0, sizeof(double) * 3 * nn, s));
     CK(cudaMemsetAsync(c->Th_prev.p, 0, sizeof(double) * 3 * nn, s));
     CK(cudaMemsetAsync(c->st.p, 0, sizeof(DevStats), s));
@@ -1018,8 +1027,13 @@ __global__ void k_particles_out(Dem D, const double* Fh, const double* Th, doubl
     q[4 * i + 2] = qq.z;
     q[4 * i + 3] = qq.w;
     for (int a = 0; a < 3; ++a) {
-        F[3 * i + a] = Fh[3 * i + a];
-        T[3 * i + a] = Th[3 * i + a];
+        double f = 0.0, t = 0.0;
+        for (int r = 0; r < NREP; ++r) {
+            f += Fh[3 * ((size_t)r * D.n + i) + a];
+            t += Th[3 * ((size_t)r * D.n + i) + a];
+        }
+        F[3 * i + a] = f;
+        T[3 * i + a] = t;
     }
 }
 
@@ -1137,7 +1151,7 @@ int lbm_dem_read_counters(lbmdem_ctx* c, int64_t out[10]) {
     out[1] = c->nS;
     out[2] = fluid;
     out[3] = c->nband;
-    out[4] = (int64_t)c->nwarps * 32;
+    out[4] = (int64_t)c->nwarps * LINK_WARP;
     out[5] = nb;
     out[6] = c->t;
     out[7] = c->relayouts;

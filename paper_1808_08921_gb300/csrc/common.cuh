@@ -170,10 +170,16 @@ struct PartView {
     const float* R;       // [n]
     const double* Rd;     // [n] radii in FP64 for the exact inside test
     const int4* org;      // [n] integer origin floor(Xref)
+    const int4* orgw;     // [n] that origin wrapped into the box (periodic axes)
     const float4* xf;     // [n] X(t) - origin, FP32
-    double* Fh;           // [n][3] hydrodynamic force accumulator
-    double* Th;           // [n][3] hydrodynamic torque accumulator
+    double* Fh;           // [NREP][n][3] hydrodynamic force accumulators (summed by the DEM)
+    double* Th;           // [NREP][n][3] hydrodynamic torque accumulators
 };
+
+// The link kernel spreads its atomics over NREP copies of each sphere's
+// force and torque accumulators (fewer same-address collisions); the DEM
+// kernel and the read-out sum the copies.
+constexpr int NREP = 8;
 
 // Exact "inside" test shared by painting and the map update: |y - X|^2 < R^2
 // in FP64 without contraction, X = Xref + dX (+ compensation).
@@ -181,6 +187,14 @@ __device__ __forceinline__ bool inside_exact(double ax, double ay, double az, do
     double s = __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az));
     return s < __dmul_rn(R, R);
 }
+
+// FP32 |a|^2 with a fixed rounding (no contraction), used identically by the
+// map update and the link kernel so that both take the same decisions.
+__device__ __forceinline__ float norm2_rn(float ax, float ay, float az) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)), __fmul_rn(az, az));
+}
+// the FP32 inside test decides only outside this relative margin of R^2
+constexpr float FP32_MARGIN = 1e-5f;
 
 // |y - X|^2 / R^2 with the same operation order and rounding as the test
 // above; among the spheres that contain a node, the smallest ratio owns it.

@@ -23,6 +23,8 @@
 // Kahan compensation term), so the substep loop needs no FP64 arithmetic.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "layout.cuh"
@@ -36,18 +38,22 @@ __device__ __forceinline__ float3 crossf(float3 a, float3 b) {
     return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
+constexpr int TEAM = 4;  // threads per sphere: they share its neighbour list
+
 // Contact forces on sphere i (Eqs. 11-12): Hertz normal force, incremental
 // Mindlin tangential force from the half-step relative velocity at the
 // contact point, previous tangential force projected on the current tangent
 // plane, Coulomb cap.  dt_inc = 0 evaluates without tangential increment.
-__device__ void contact_forces(const Dem& D, int i, int b, float dt_inc, float3& F, float3& T) {
+// Lane `tl` of the sphere's team takes entries tl, tl + TEAM, ...; the
+// caller reduces over the team.
+__device__ void contact_forces(const Dem& D, int i, int b, float dt_inc, int tl, float3& F, float3& T) {
+    F = make_float3(0.f, 0.f, 0.f);
+    T = make_float3(0.f, 0.f, 0.f);
     float4 xi4 = __ldcg(&D.dXb[b * D.n + i]);
     float3 xi = f3(xi4), vi = f3(__ldcg(&D.Vhb[b * D.n + i])), wi = f3(__ldcg(&D.Whb[b * D.n + i]));
     float Ri = D.R[i];
-    F = make_float3(0.f, 0.f, 0.f);
-    T = make_float3(0.f, 0.f, 0.f);
     int cnt = D.nb_cnt[i];
-    for (int k = 0; k < cnt; ++k) {
+    for (int k = tl; k < cnt; k += TEAM) {
         size_t e = (size_t)i * D.nbmax + k;
         int j = D.nb_j[e];
         float4 dr = D.nb_dref[e];
@@ -101,10 +107,26 @@ __device__ void contact_forces(const Dem& D, int i, int b, float dt_inc, float3&
     }
 }
 
+// sum over the TEAM lanes of a sphere (lanes of a team are consecutive)
+__device__ __forceinline__ void team_sum(float3& F, float3& T) {
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int o = 1; o < TEAM; o <<= 1) {
+        F.x += __shfl_xor_sync(full, F.x, o);
+        F.y += __shfl_xor_sync(full, F.y, o);
+        F.z += __shfl_xor_sync(full, F.z, o);
+        T.x += __shfl_xor_sync(full, T.x, o);
+        T.y += __shfl_xor_sync(full, T.y, o);
+        T.z += __shfl_xor_sync(full, T.z, o);
+    }
+}
+
 __global__ void k_dem_step(Dem D, int init_only) {
     cg::cluster_group cl = cg::this_cluster();
     const int nth = gridDim.x * blockDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int team = tid / TEAM, tl = tid % TEAM, nteams = nth / TEAM;
+    const int iters = (D.n + nteams - 1) / nteams;  // uniform: shuffles stay converged
     const float dt = D.dt;
     if (init_only) {
         for (int i = tid; i < D.n; i += nth) {
@@ -113,20 +135,26 @@ __global__ void k_dem_step(Dem D, int init_only) {
             D.Whb[i] = D.W[i];
         }
         cl.sync();
-        for (int i = tid; i < D.n; i += nth) {
-            float3 F, T;
-            contact_forces(D, i, 0, 0.f, F, T);
-            D.Fc[i] = make_float4(F.x, F.y, F.z, 0.f);
-            D.Tc[i] = make_float4(T.x, T.y, T.z, 0.f);
-        }
-    }
-    if (!init_only) {
-        for (int i = tid; i < D.n; i += nth) {
-            double f[3], t[3];
-            for (int a = 0; a < 3; ++a) {
-                f[a] = D.Fh[3 * i + a];
-                t[a] = D.Th[3 * i + a];
+        for (int it = 0; it < iters; ++it) {
+            int i = team + it * nteams;
+            float3 F = make_float3(0.f, 0.f, 0.f), T = F;
+            if (i < D.n) contact_forces(D, i, 0, 0.f, tl, F, T);
+            team_sum(F, T);
+            if (i < D.n && tl == 0) {
+                D.Fc[i] = make_float4(F.x, F.y, F.z, 0.f);
+                D.Tc[i] = make_float4(T.x, T.y, T.z, 0.f);
             }
+        }
+    } else {
+        for (int it = 0; it < iters; ++it) {
+            int i = team + it * nteams;
+            if (i >= D.n || tl != 0) continue;
+            double f[3] = {0.0, 0.0, 0.0}, t[3] = {0.0, 0.0, 0.0};
+            for (int r = 0; r < NREP; ++r)
+                for (int a = 0; a < 3; ++a) {
+                    f[a] += D.Fh[3 * ((size_t)r * D.n + i) + a];
+                    t[a] += D.Th[3 * ((size_t)r * D.n + i) + a];
+                }
             D.Fa[i] = make_float4((float)(0.5 * (f[0] + D.Fh_prev[3 * i])), (float)(0.5 * (f[1] + D.Fh_prev[3 * i + 1])),
                                   (float)(0.5 * (f[2] + D.Fh_prev[3 * i + 2])), 0.f);
             D.Ta[i] = make_float4((float)(0.5 * (t[0] + D.Th_prev[3 * i])), (float)(0.5 * (t[1] + D.Th_prev[3 * i + 1])),
@@ -139,7 +167,11 @@ __global__ void k_dem_step(Dem D, int init_only) {
     }
     for (int s = 0; s < (init_only ? 0 : D.K); ++s) {
         const int b = s & 1;
-        for (int i = tid; i < D.n; i += nth) {
+        // kick + drift of the own spheres (lane 0 of each sphere's team owns
+        // every per-sphere update, so no barrier is needed between substeps)
+        for (int it = 0; it < iters; ++it) {
+            int i = team + it * nteams;
+            if (i >= D.n || tl != 0) continue;
             float4 dx = D.dX[i];
             float4 vh, wh;
             if (D.fixed[i]) {
@@ -148,13 +180,11 @@ __global__ void k_dem_step(Dem D, int init_only) {
                 float4 fc = D.Fc[i], tc = D.Tc[i], v = D.V[i], w = D.W[i];
                 float im = D.invm[i], iI = D.invI[i];
                 float4 fa = D.Fa[i], ta = D.Ta[i];
-                float fhx = fa.x, fhy = fa.y, fhz = fa.z;
-                float thx = ta.x, thy = ta.y, thz = ta.z;
-                vh = make_float4(v.x + 0.5f * dt * (fc.x + fhx + D.g.x) * im,
-                                 v.y + 0.5f * dt * (fc.y + fhy + D.g.y) * im,
-                                 v.z + 0.5f * dt * (fc.z + fhz + D.g.z) * im, 0.f);
-                wh = make_float4(w.x + 0.5f * dt * (tc.x + thx) * iI, w.y + 0.5f * dt * (tc.y + thy) * iI,
-                                 w.z + 0.5f * dt * (tc.z + thz) * iI, 0.f);
+                vh = make_float4(v.x + 0.5f * dt * (fc.x + fa.x + D.g.x) * im,
+                                 v.y + 0.5f * dt * (fc.y + fa.y + D.g.y) * im,
+                                 v.z + 0.5f * dt * (fc.z + fa.z + D.g.z) * im, 0.f);
+                wh = make_float4(w.x + 0.5f * dt * (tc.x + ta.x) * iI, w.y + 0.5f * dt * (tc.y + ta.y) * iI,
+                                 w.z + 0.5f * dt * (tc.z + ta.z) * iI, 0.f);
                 // drift with Kahan-compensated FP32 accumulation
                 float4 c = D.dXc[i];
                 float yx = dt * vh.x - c.x, yy = dt * vh.y - c.y, yz = dt * vh.z - c.z;
@@ -178,32 +208,38 @@ __global__ void k_dem_step(Dem D, int init_only) {
             D.Whb[b * D.n + i] = wh;
         }
         cl.sync();
-        for (int i = tid; i < D.n; i += nth) {
-            if (D.fixed[i]) {
-                D.V[i] = D.W[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                continue;
+        // contact forces (a team per sphere) and the closing kick
+        for (int it = 0; it < iters; ++it) {
+            int i = team + it * nteams;
+            bool act = i < D.n && !D.fixed[i];
+            float3 F = make_float3(0.f, 0.f, 0.f), T = F;
+            if (act) contact_forces(D, i, b, dt, tl, F, T);
+            team_sum(F, T);
+            if (i < D.n && tl == 0) {
+                if (!act) {
+                    D.V[i] = D.W[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    continue;
+                }
+                D.Fc[i] = make_float4(F.x, F.y, F.z, 0.f);
+                D.Tc[i] = make_float4(T.x, T.y, T.z, 0.f);
+                float4 vh = D.Vhb[b * D.n + i], wh = D.Whb[b * D.n + i];
+                float im = D.invm[i], iI = D.invI[i];
+                float4 fa = D.Fa[i], ta = D.Ta[i];
+                D.V[i] = make_float4(vh.x + 0.5f * dt * (F.x + fa.x + D.g.x) * im,
+                                     vh.y + 0.5f * dt * (F.y + fa.y + D.g.y) * im,
+                                     vh.z + 0.5f * dt * (F.z + fa.z + D.g.z) * im, 0.f);
+                D.W[i] = make_float4(wh.x + 0.5f * dt * (T.x + ta.x) * iI, wh.y + 0.5f * dt * (T.y + ta.y) * iI,
+                                     wh.z + 0.5f * dt * (T.z + ta.z) * iI, 0.f);
             }
-            float3 F, T;
-            contact_forces(D, i, b, dt, F, T);
-            D.Fc[i] = make_float4(F.x, F.y, F.z, 0.f);
-            D.Tc[i] = make_float4(T.x, T.y, T.z, 0.f);
-            float4 vh = D.Vhb[b * D.n + i], wh = D.Whb[b * D.n + i];
-            float im = D.invm[i], iI = D.invI[i];
-            float4 fa = D.Fa[i], ta = D.Ta[i];
-            float fhx = fa.x, fhy = fa.y, fhz = fa.z;
-            float thx = ta.x, thy = ta.y, thz = ta.z;
-            D.V[i] = make_float4(vh.x + 0.5f * dt * (F.x + fhx + D.g.x) * im,
-                                 vh.y + 0.5f * dt * (F.y + fhy + D.g.y) * im,
-                                 vh.z + 0.5f * dt * (F.z + fhz + D.g.z) * im, 0.f);
-            D.W[i] = make_float4(wh.x + 0.5f * dt * (T.x + thx) * iI, wh.y + 0.5f * dt * (T.y + thy) * iI,
-                                 wh.z + 0.5f * dt * (T.z + thz) * iI, 0.f);
         }
     }
     // outputs of the step: lattice frame of every sphere, displacement and
     // speed maxima for the re-layout decision, NaN / skin checks
     float dmax = 0.f, vmax = 0.f;
     uint32_t bad = 0;
-    for (int i = tid; i < D.n; i += nth) {
+    for (int it = 0; it < iters; ++it) {
+        int i = team + it * nteams;
+        if (i >= D.n || tl != 0) continue;
         float4 dx = D.dX[i], c = D.dXc[i], v = D.V[i];
         double X0 = D.Xref[3 * i] + (double)dx.x - (double)c.x;
         double X1 = D.Xref[3 * i + 1] + (double)dx.y - (double)c.y;
@@ -211,6 +247,10 @@ __global__ void k_dem_step(Dem D, int init_only) {
         int4 o = make_int4((int)floor(D.Xref[3 * i]), (int)floor(D.Xref[3 * i + 1]),
                            (int)floor(D.Xref[3 * i + 2]), 0);
         D.org[i] = o;
+        int wx = D.px ? (int)(((long long)o.x % (long long)D.Lx + (long long)D.Lx) % (long long)D.Lx) : o.x;
+        int wy = (int)(((long long)o.y % (long long)D.Ly + (long long)D.Ly) % (long long)D.Ly);
+        int wz = (int)(((long long)o.z % (long long)D.Lz + (long long)D.Lz) % (long long)D.Lz);
+        D.orgw[i] = make_int4(wx, wy, wz, 0);
         D.xf[i] = make_float4((float)(X0 - o.x), (float)(X1 - o.y), (float)(X2 - o.z), 0.f);
         float dd = sqrtf(dx.x * dx.x + dx.y * dx.y + dx.z * dx.z);
         float vv = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
@@ -236,13 +276,13 @@ __global__ void k_dem_step(Dem D, int init_only) {
 }
 
 void launch_dem_step(const Dem& D, bool init_only, cudaStream_t s) {
-    int C = D.cluster;
-    int T = 256;
-    if (D.n <= 256) {
-        C = 1;
-        T = D.n <= 32 ? 32 : ((D.n + 31) / 32) * 32;
-    } else if (D.n > C * 256) {
-        T = (D.n + C - 1) / C;
+    // TEAM threads per sphere, up to 8 CTAs of up to 1024 threads
+    long long need = (long long)TEAM * (D.n > 0 ? D.n : 1);
+    int C = 1;
+    int T = (int)(((need + 31) / 32) * 32);
+    if (T > 256) {
+        C = (int)std::min<long long>(D.cluster, (need + 255) / 256);
+        T = (int)((need + C - 1) / C);
         T = ((T + 31) / 32) * 32;
         if (T > 1024) T = 1024;
     }
@@ -491,6 +531,7 @@ __global__ void k_band_cand(BandCand B) {
         }
     }
     B.cand[k] = make_int4(c4[0], c4[1], c4[2], c4[3]);
+    if (B.band_dense) B.band_dense[((size_t)x * B.ny + y) * B.nz + z] = nfound >= 2 ? 2 : 1;
 }
 
 void launch_band_cand(const BandCand& B, cudaStream_t s) {

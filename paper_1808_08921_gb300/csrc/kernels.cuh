@@ -28,11 +28,23 @@ struct BC {
     const unsigned long long* t_dev;
 };
 
-// Per-particle surface lists for the link kernel: entries {cidx, coord},
-// each particle's run padded to a multiple of 32 (one warp = one particle).
+// Link lists for the link kernel, grouped by (sphere, direction) and padded
+// to LINK_WARP records, so a warp walks LINK_WARP links of one sphere in one
+// direction (LINK_WARP / 32 per thread):
+//   warp_pd[w] = sphere << 5 | direction m  (the solid neighbour is x + c_m)
+//   link[k]    = {cidx of the fluid node x,
+//                 (x - org) + 128 packed 8 bits per axis | maybe << 24 |
+//                 shared << 25}
+// `maybe` marks a neighbour inside a band: whether the sphere owns it now
+// is decided by the map update's FP32 test (same operands and rounding),
+// or by reading the owner map near the FP32 margin or when the band node
+// has several candidate spheres (`shared`).  The other links are fixed until
+// the next re-layout.  cidx == NONE pads.
+constexpr int LINK_WARP = 128;
+
 struct LinkLists {
-    const uint2* ent;
-    const int32_t* warp_part;
+    const uint2* link;
+    const uint32_t* warp_pd;
     uint32_t nwarps;
 };
 
@@ -92,6 +104,7 @@ struct Dem {
     float4* nb_ft;           // tangential history (force on i)
     // outputs for the lattice kernels
     int4* org;
+    int4* orgw;
     float4* xf;
     uint32_t* status;
     uint32_t* max_disp_bits;

@@ -157,21 +157,94 @@ __global__ void __launch_bounds__(256) k_collide_even(Lat L, Mon mon) {
     mon_flush<MON>(a, mon, true);
 }
 
+// compact index of bit `bit` of a word record if that node is fluid now
+__device__ __forceinline__ uint32_t word_index(const uint4& r, const uint32_t* mBp, uint32_t bit) {
+    if (!(r.x & bit)) return NONE;
+    uint32_t low = bit - 1u;
+    if (r.y & bit) return r.z + __popc(r.y & low);
+    return r.w + __popc(__ldg(mBp) & low);
+}
+
+// Neighbours x + c_m of node (x, y, z) on the z-line (xs, ys): the record of
+// the word holding z serves dz = -1, 0, +1 unless z +- 1 crosses a word.
+struct LineProbe {
+    const Lat& L;
+    size_t wl;
+    int w0;
+    uint4 r0;
+    __device__ __forceinline__ LineProbe(const Lat& L_, int xs, int ys, int z) : L(L_) {
+        wl = ((size_t)xs * L.ny + ys) * L.nw;
+        w0 = z >> 5;
+        r0 = __ldg(&L.rec[wl + w0]);
+    }
+    __device__ __forceinline__ uint32_t at(int zs) const {
+        int wz = zs >> 5;
+        uint4 r = wz == w0 ? r0 : __ldg(&L.rec[wl + wz]);
+        return word_index(r, &L.maskB[wl + wz], 1u << (zs & 31));
+    }
+};
+
 // Odd step: node x gathers direction m from slot opp(m) of x - c_m (or from
 // its own slot m when x - c_m is solid or outside), collides, and scatters
 // direction m to slot m of x + c_m (or its own slot opp(m)).  Each thread
 // reads and writes the same 19 locations, so the update is in place.
 template <bool MON>
-__global__ void __launch_bounds__(256) k_collide_odd(Lat L, Mon mon) {
+__global__ void __launch_bounds__(256, 3) k_collide_odd(Lat L, Mon mon) {
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     MonAcc a = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     bool active = i < L.nS && fluid_bit(L, i);
     if (active) {
         int x, y, z;
         unpack_coord(__ldcs(&L.coord[i]), x, y, z);
+        const int zm = z == 0 ? L.nz - 1 : z - 1, zp = z == L.nz - 1 ? 0 : z + 1;
+        const int ym = y == 0 ? L.ny - 1 : y - 1, yp = y == L.ny - 1 ? 0 : y + 1;
+        int xm = x - 1, xp = x + 1;
+        bool hasm = true, hasp = true;
+        if (L.px) {
+            xm = x == 0 ? L.nx - 1 : xm;
+            xp = x == L.nx - 1 ? 0 : xp;
+        } else {
+            hasm = x > 0;
+            hasp = x < L.nx - 1;
+        }
         uint32_t nb[Q - 1];  // compact index of x + c_m, or NONE
-#pragma unroll
-        for (int m = 0; m < Q - 1; ++m) nb[m] = fluid_index(L, x, y, z, cx(m), cy(m), cz(m));
+        {
+            LineProbe l(L, x, y, z);
+            nb[4] = l.at(zp);
+            nb[5] = l.at(zm);
+        }
+        {
+            LineProbe l(L, x, yp, z);
+            nb[2] = l.at(z);
+            nb[14] = l.at(zp);
+            nb[15] = l.at(zm);
+        }
+        {
+            LineProbe l(L, x, ym, z);
+            nb[3] = l.at(z);
+            nb[16] = l.at(zp);
+            nb[17] = l.at(zm);
+        }
+        if (hasp) {
+            LineProbe l(L, xp, y, z);
+            nb[0] = l.at(z);
+            nb[8] = l.at(zp);
+            nb[9] = l.at(zm);
+            nb[6] = LineProbe(L, xp, yp, z).at(z);
+            nb[7] = LineProbe(L, xp, ym, z).at(z);
+        } else {
+            nb[0] = nb[8] = nb[9] = nb[6] = nb[7] = NONE;
+        }
+        if (hasm) {
+            LineProbe l(L, xm, y, z);
+            nb[1] = l.at(z);
+            nb[12] = l.at(zp);
+            nb[13] = l.at(zm);
+            nb[10] = LineProbe(L, xm, yp, z).at(z);
+            nb[11] = LineProbe(L, xm, ym, z).at(z);
+        } else {
+            nb[1] = nb[12] = nb[13] = nb[10] = nb[11] = NONE;
+        }
         float g[Q];
 #pragma unroll
         for (int m = 0; m < Q - 1; ++m) {

@@ -228,10 +228,18 @@ __global__ void k_band_collect(LayoutArgs A, uint32_t* band_coord, uint32_t* cou
     if (k < cap) band_coord[k] = pack_coord(x, y, z);
 }
 
-// surface-node lists: every stored node within R + skin + sqrt(2) of a
-// sphere (all neighbours that the sphere can own before the next re-layout)
+// link lists: for every stored node x within R + skin + 1.5 of a sphere and
+// every direction m, a link if x + c_m is owned by the sphere and outside
+// every band (fixed until the next re-layout), or a `maybe` link if x + c_m
+// is a band node within R + skin of the sphere (owner read each step).
+struct SurfNode {
+    uint32_t ci;
+    int ox, oy, oz;           // x - floor(Xref)
+    uint32_t sure, maybe, shared;
+};
+
 __device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, long long t, int x0, int y0, int z0,
-                                          int ey, int ez, uint32_t& cidx, uint32_t& coord) {
+                                          int ey, int ez, SurfNode& sn) {
     int zi = z0 + (int)(t % ez);
     long long r = t / ez;
     int yi = y0 + (int)(r % ey);
@@ -243,17 +251,45 @@ __device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, long long t,
         x = xi;
     }
     int y = wrapi(yi, A.L.ny), z = wrapi(zi, A.L.nz);
-    double ax = (double)xi - A.X[3 * p], ay = (double)yi - A.X[3 * p + 1], az = (double)zi - A.X[3 * p + 2];
-    double reach = A.R[p] + A.reach_extra;
+    double X0 = A.X[3 * p], X1 = A.X[3 * p + 1], X2 = A.X[3 * p + 2];
+    double ax = (double)xi - X0, ay = (double)yi - X1, az = (double)zi - X2;
+    double Rp = A.R[p];
+    double reach = Rp + A.reach_extra;
     if (ax * ax + ay * ay + az * az >= reach * reach) return false;
     bool fl;
     uint32_t ci = stored_index(A.L, x, y, z, fl);
     if (ci == NONE) return false;
-    cidx = ci;
-    coord = pack_coord(x, y, z);
+    double Rb = Rp + A.skin;
+    uint32_t sure = 0, maybe = 0, shared = 0;
+#pragma unroll
+    for (int m = 0; m < Q - 1; ++m) {
+        int xs = x + cx(m);
+        if (A.L.px) xs = wrapi(xs, A.L.nx);
+        else if (xs < 0 || xs >= A.L.nx) continue;
+        int ys = wrapi(y + cy(m), A.L.ny), zs = wrapi(z + cz(m), A.L.nz);
+        size_t li = ((size_t)xs * A.L.ny + ys) * A.L.nz + zs;
+        if (A.band[li]) {
+            double bx = ax + cx(m), by = ay + cy(m), bz = az + cz(m);
+            if (bx * bx + by * by + bz * bz < Rb * Rb) {
+                maybe |= 1u << m;
+                if (A.band[li] >= 2) shared |= 1u << m;
+            }
+        } else if (A.owner[li] == p) {
+            sure |= 1u << m;
+        }
+    }
+    if (!(sure | maybe)) return false;
+    sn.ci = ci;
+    sn.ox = xi - (int)floor(X0);
+    sn.oy = yi - (int)floor(X1);
+    sn.oz = zi - (int)floor(X2);
+    sn.sure = sure;
+    sn.maybe = maybe;
+    sn.shared = shared;
     return true;
 }
 
+// per sphere: links per direction (padded to whole warps)
 __global__ void k_surf_count(SurfArgs A) {
     int p = blockIdx.x;
     double reach = A.R[p] + A.reach_extra;
@@ -262,22 +298,23 @@ __global__ void k_surf_count(SurfArgs A) {
     int z0 = (int)ceil(A.X[3 * p + 2] - reach), z1 = (int)floor(A.X[3 * p + 2] + reach);
     int ey = y1 - y0 + 1, ez = z1 - z0 + 1;
     long long vol = (long long)(x1 - x0 + 1) * ey * ez;
-    uint32_t c = 0;
-    for (long long t = threadIdx.x; t < vol; t += blockDim.x) {
-        uint32_t ci, co;
-        if (surf_node(A, p, t, x0, y0, z0, ey, ez, ci, co)) ++c;
-    }
-    __shared__ uint32_t sh[32];
-    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+    __shared__ uint32_t cnt[Q - 1];
+    if (threadIdx.x < Q - 1) cnt[threadIdx.x] = 0;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t s = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
-        A.count[p] = (s + 31u) & ~31u;  // padded to whole warps
+    for (long long t = threadIdx.x; t < vol; t += blockDim.x) {
+        SurfNode sn;
+        if (!surf_node(A, p, t, x0, y0, z0, ey, ez, sn)) continue;
+        uint32_t bits = sn.sure | sn.maybe;
+        for (int m = 0; m < Q - 1; ++m)
+            if (bits >> m & 1u) atomicAdd(&cnt[m], 1u);
     }
+    __syncthreads();
+    if (threadIdx.x < Q - 1)
+        A.count[(size_t)p * (Q - 1) + threadIdx.x] = (cnt[threadIdx.x] + (LINK_WARP - 1)) / LINK_WARP * LINK_WARP;
 }
 
+// fill in a deterministic order: per direction, chunks of blockDim nodes in
+// bounding-box order, block prefix sums over the chunk
 __global__ void k_surf_fill(SurfArgs A) {
     int p = blockIdx.x;
     double reach = A.R[p] + A.reach_extra;
@@ -286,43 +323,55 @@ __global__ void k_surf_fill(SurfArgs A) {
     int z0 = (int)ceil(A.X[3 * p + 2] - reach), z1 = (int)floor(A.X[3 * p + 2] + reach);
     int ey = y1 - y0 + 1, ez = z1 - z0 + 1;
     long long vol = (long long)(x1 - x0 + 1) * ey * ez;
-    uint32_t base = A.offset[p];
-    uint32_t end = base + A.count[p];
-    __shared__ uint32_t sh[33];
-    __shared__ uint32_t run;
-    if (threadIdx.x == 0) run = 0;
+    __shared__ uint32_t sh[Q - 1][33];
+    __shared__ uint32_t run[Q - 1];
+    if (threadIdx.x < Q - 1) run[threadIdx.x] = 0;
     __syncthreads();
-    // deterministic order: chunks of blockDim nodes, block prefix sum per chunk
+    uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (long long t0 = 0; t0 < vol; t0 += blockDim.x) {
         long long t = t0 + threadIdx.x;
-        uint32_t ci = 0, co = 0;
-        bool ok = t < vol && surf_node(A, p, t, x0, y0, z0, ey, ez, ci, co);
-        unsigned bal = __ballot_sync(0xffffffffu, ok);
-        uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        uint32_t before = __popc(bal & ((1u << lane) - 1u));
-        if (lane == 0) sh[wid] = __popc(bal);
+        SurfNode sn;
+        bool ok = t < vol && surf_node(A, p, t, x0, y0, z0, ey, ez, sn);
+        uint32_t bits = ok ? (sn.sure | sn.maybe) : 0u;
+        uint32_t before[Q - 1];
+        for (int m = 0; m < Q - 1; ++m) {
+            unsigned bal = __ballot_sync(0xffffffffu, (bits >> m) & 1u);
+            before[m] = __popc(bal & ((1u << lane) - 1u));
+            if (lane == 0) sh[m][wid] = __popc(bal);
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < Q - 1) {
             uint32_t s = 0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-                uint32_t c = sh[k];
-                sh[k] = s;
+            for (uint32_t k = 0; k < nwarp; ++k) {
+                uint32_t c = sh[threadIdx.x][k];
+                sh[threadIdx.x][k] = s;
                 s += c;
             }
-            sh[32] = s;
+            sh[threadIdx.x][32] = s;
         }
         __syncthreads();
-        if (ok) {
-            uint32_t pos = base + run + sh[wid] + before;
-            A.ent[pos] = make_uint2(ci, co);
+        if (bits) {
+            uint32_t rel = (uint32_t)(sn.ox + 128) | ((uint32_t)(sn.oy + 128) << 8) |
+                           ((uint32_t)(sn.oz + 128) << 16);
+            for (int m = 0; m < Q - 1; ++m) {
+                if (!(bits >> m & 1u)) continue;
+                size_t g = (size_t)p * (Q - 1) + m;
+                uint32_t pos = A.offset[g] + run[m] + sh[m][wid] + before[m];
+                A.link[pos] = make_uint2(sn.ci, rel | ((sn.maybe >> m & 1u) << 24) | ((sn.shared >> m & 1u) << 25));
+            }
         }
         __syncthreads();
-        if (threadIdx.x == 0) run += sh[32];
+        if (threadIdx.x < Q - 1) run[threadIdx.x] += sh[threadIdx.x][32];
         __syncthreads();
     }
-    // pad to the warp boundary and tag the warps with their sphere
-    for (uint32_t k = base + run + threadIdx.x; k < end; k += blockDim.x) A.ent[k] = make_uint2(NONE, 0u);
-    for (uint32_t k = base / 32 + threadIdx.x; k < end / 32; k += blockDim.x) A.warp_part[k] = p;
+    // pad each (sphere, direction) group and tag its warps
+    for (int m = 0; m < Q - 1; ++m) {
+        size_t g = (size_t)p * (Q - 1) + m;
+        uint32_t base = A.offset[g], end = base + A.count[g];
+        for (uint32_t k = base + run[m] + threadIdx.x; k < end; k += blockDim.x) A.link[k] = make_uint2(NONE, 0u);
+        for (uint32_t k = base / LINK_WARP + threadIdx.x; k < end / LINK_WARP; k += blockDim.x)
+            A.warp_pd[k] = ((uint32_t)p << 5) | (uint32_t)m;
+    }
 }
 
 __global__ void k_fill_u64(unsigned long long* p, unsigned long long v, size_t n) {

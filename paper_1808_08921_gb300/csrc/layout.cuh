@@ -33,10 +33,13 @@ struct SurfArgs {
     const double* X;
     const double* R;
     double reach_extra;
-    uint32_t* count;
-    const uint32_t* offset;
-    uint2* ent;
-    int32_t* warp_part;
+    double skin;
+    const int32_t* owner;   // map at layout time
+    const uint8_t* band;    // band flags at layout time
+    uint32_t* count;        // [n * 18] links per (sphere, direction), padded to 32
+    const uint32_t* offset; // exclusive scan of count
+    uint2* link;
+    uint32_t* warp_pd;
 };
 
 struct CellGrid {
@@ -77,6 +80,8 @@ struct BandCand {
     int4* cand;
     uint32_t n;
     uint32_t* status;
+    uint8_t* band_dense;   // per lattice node: 1 = one candidate sphere, 2 = several
+    int nx, ny, nz;
 };
 
 void fill_i32(int32_t* p, int32_t v, size_t n, cudaStream_t s);
