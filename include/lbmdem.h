@@ -153,6 +153,27 @@ int lbm_dem_read_fields(lbmdem_ctx* c, double* rho, double* u, uint8_t* solid);
 int lbm_dem_read_particles(lbmdem_ctx* c, double* X, double* V, double* Omega, double* quat,
                            double* F_hyd, double* T_hyd);
 
+/* The same read-out without any allocation (the paper has no counterpart:
+ * this serves callers that cannot allocate device memory at read time, such
+ * as one whose device memory is committed to the lattice state, where a
+ * cudaMalloc fails, or one that must not take the device-wide
+ * synchronisation of cudaFree while other streams are busy).  Same
+ * arguments, layouts and results as lbm_dem_read_particles; the values are
+ * staged in a fixed device array of the library (19 doubles per sphere,
+ * 9.5 MiB) instead of a buffer allocated per call.
+ *  - At most 65536 spheres: a larger packing returns LBMDEM_ERR_CAPACITY
+ *    with a message, and nothing is read.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before any
+ *    stream capture on the device.
+ *  - The array is shared by all calls on a device and keeps the last call's
+ *    contents (every value copied out is written by the same call).  Calls
+ *    whose GPU work overlaps (two contexts of one device used from two host
+ *    threads) race on it.
+ * Synchronises the context stream. */
+int lbm_dem_read_particles_noalloc(lbmdem_ctx* c, double* X, double* V, double* Omega,
+                                   double* quat, double* F_hyd, double* T_hyd);
+
 /* Probe trace: trace[k] = mean density over the fluid nodes of plane probe_x
  * entering step k (after that step's map update), k = 0 .. len-1.  Copies
  * min(len, max_len) values; *len receives the full length.  Synchronises. */

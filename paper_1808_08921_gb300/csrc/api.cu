@@ -16,6 +16,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1198,3 +1199,75 @@ void lbm_dem_destroy(lbmdem_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Sphere read-out that allocates nothing.
+//
+// lbm_dem_read_particles stages its output in a device buffer that it
+// cudaMallocs and cudaFrees on every call.  Two kinds of caller cannot do
+// that: one whose device memory is committed to the lattice state down to
+// the last few MB (the cudaMalloc fails), and one that reads the spheres
+// while other streams of the process keep the GPU busy and cannot take the
+// device-wide synchronisation of cudaFree.  This variant runs the same
+// read-out kernel into a fixed file-scope device array and copies from there
+// straight into the caller's host arrays.
+//
+// The array is shared by every call in the process on a given device and
+// keeps the last call's contents; nothing in it needs clearing, because the
+// kernel writes every value that the call copies out.  Two calls whose work
+// overlaps on the GPU (two contexts of one device driven from two host
+// threads) race on it.
+namespace {
+constexpr int NOALLOC_MAX_SPHERES = 65536;  // 19 doubles each: 9.5 MiB
+constexpr int NOALLOC_MAX_DEVICES = 64;
+__device__ __align__(256) double noalloc_particle_scratch[19 * NOALLOC_MAX_SPHERES];
+
+std::mutex noalloc_mutex;
+double* noalloc_scratch_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the array on device `dev` (which must be current),
+// looked up once per device on the first call.
+int noalloc_scratch(lbmdem_ctx* c, int dev, double** out) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return fail(c, LBMDEM_ERR_INVALID_ARG, "read_particles_noalloc: device %d beyond %d", dev,
+                    NOALLOC_MAX_DEVICES);
+    std::lock_guard<std::mutex> lock(noalloc_mutex);
+    if (!noalloc_scratch_ptr[dev]) {
+        double* p = nullptr;
+        CK(cudaGetSymbolAddress((void**)&p, noalloc_particle_scratch));
+        noalloc_scratch_ptr[dev] = p;
+    }
+    *out = noalloc_scratch_ptr[dev];
+    return 0;
+}
+}  // namespace
+
+extern "C" int lbm_dem_read_particles_noalloc(lbmdem_ctx* c, double* X, double* V, double* Om, double* quat,
+                                              double* F_hyd, double* T_hyd) {
+    if (!c) return LBMDEM_ERR_INVALID_ARG;
+    if (!c->have_packing) return fail(c, LBMDEM_ERR_STATE, "no packing");
+    if (c->np == 0) return 0;
+    if (c->np > NOALLOC_MAX_SPHERES)
+        return fail(c, LBMDEM_ERR_CAPACITY,
+                    "read_particles_noalloc: %d spheres exceed its fixed buffer of %d spheres "
+                    "(use lbm_dem_read_particles)",
+                    (int)c->np, NOALLOC_MAX_SPHERES);
+    CK(cudaSetDevice(c->p.device));
+    double* d = nullptr;
+    if (int r = noalloc_scratch(c, c->p.device, &d)) return r;
+    size_t n = c->np;
+    Dem D = make_dem(c);
+    k_particles_out<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(D, c->Fh.p, c->Th.p, d, d + 3 * n,
+                                                                      d + 6 * n, d + 9 * n, d + 13 * n,
+                                                                      d + 16 * n);
+    CK(cudaGetLastError());
+    double* dst[6] = {X, V, Om, quat, F_hyd, T_hyd};
+    const size_t off[6] = {0, 3 * n, 6 * n, 9 * n, 13 * n, 16 * n};
+    const size_t len[6] = {3 * n, 3 * n, 3 * n, 4 * n, 3 * n, 3 * n};
+    for (int k = 0; k < 6; ++k)
+        if (dst[k])
+            CK(cudaMemcpyAsync(dst[k], d + off[k], sizeof(double) * len[k], cudaMemcpyDeviceToHost,
+                               c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return lbm_dem_status(c);
+}

@@ -25,7 +25,8 @@ ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "UNSTABLE", -5:
 # every symbol include/lbmdem.h declares
 SYMBOLS = ("lbm_dem_default_params", "lbm_dem_init", "lbm_dem_set_packing",
            "lbm_dem_set_pressure_source", "lbm_dem_step", "lbm_dem_relayout", "lbm_dem_status",
-           "lbm_dem_read_fields", "lbm_dem_read_particles", "lbm_dem_read_probe",
+           "lbm_dem_read_fields", "lbm_dem_read_particles", "lbm_dem_read_particles_noalloc",
+           "lbm_dem_read_probe",
            "lbm_dem_read_monitors", "lbm_dem_read_counters", "lbm_dem_set_timing",
            "lbm_dem_read_timing", "lbm_dem_last_error", "lbm_dem_destroy")
 
@@ -79,6 +80,7 @@ def load(build_if_missing: bool = True):
     lib.lbm_dem_relayout.argtypes = [vp]
     lib.lbm_dem_read_fields.argtypes = [vp, P(d), P(d), P(C.c_uint8)]
     lib.lbm_dem_read_particles.argtypes = [vp, P(d), P(d), P(d), P(d), P(d), P(d)]
+    lib.lbm_dem_read_particles_noalloc.argtypes = [vp, P(d), P(d), P(d), P(d), P(d), P(d)]
     lib.lbm_dem_read_probe.argtypes = [vp, P(d), i64, P(i64)]
     lib.lbm_dem_read_monitors.argtypes = [vp, P(d)]
     lib.lbm_dem_read_counters.argtypes = [vp, P(i64)]
@@ -186,6 +188,16 @@ class Sim:
         out = {k: np.zeros((n, 3)) for k in ("X", "V", "W", "Fh", "Th")}
         out["q"] = np.zeros((n, 4))
         self._check(load().lbm_dem_read_particles(
+            self._h, *[_dp(out[k]) for k in ("X", "V", "W", "q", "Fh", "Th")]))
+        return {k: v[:self.np] for k, v in out.items()}
+
+    def particles_noalloc(self):
+        """particles() through lbm_dem_read_particles_noalloc: no device memory
+        is allocated; at most 65536 spheres."""
+        n = max(self.np, 1)
+        out = {k: np.zeros((n, 3)) for k in ("X", "V", "W", "Fh", "Th")}
+        out["q"] = np.zeros((n, 4))
+        self._check(load().lbm_dem_read_particles_noalloc(
             self._h, *[_dp(out[k]) for k in ("X", "V", "W", "q", "Fh", "Th")]))
         return {k: v[:self.np] for k, v in out.items()}
 
