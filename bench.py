@@ -8,13 +8,16 @@ sinusoidal inlet (amplitude 1e-3, period 400), seeded jitter 1e-3 R, FP32
 populations; synthetic input from workloads.config_scale().
 
 metric: coupled-step MLUPS over fluid nodes (fluid-node updates per second,
-millions), whole job.  The `roofline` object is for the dominant kernel,
-collide+stream (both AA parities), at 152 algorithmic bytes per fluid node
-(19 FP32 populations read and written), its duration taken with CUDA events
-around every launch inside the timed region.  `e2e` times the same workload
-through the C ABI from host buffers: set_packing (host -> device), the K
-steps, and the read-back of the sphere state and the probe trace
-(device -> host).  `cpu_baseline` times the FP64 oracle on a few steps of the
+millions), whole job.  `kernel_rooflines` gives, for the HBM-bound kernel
+groups, the algorithmic bytes per launch (collide+stream, both AA parities:
+152 B per fluid node, 19 FP32 populations read and written; links: 8 B per
+link record, one population read and the bounced value written) over the
+group's mean launch time, taken with CUDA events around every launch inside
+the timed region; `roofline` is the one with the longest launches, and
+`step_roofline` is the whole coupled step at 152 B per fluid node.
+`e2e` times the same workload through the C ABI from host buffers:
+set_packing (host -> device, the layout build included), the K steps, and
+the read-back of the sphere state (device -> host).  `cpu_baseline` times the FP64 oracle on a few steps of the
 same workload on the host cores.  Multi-GPU (torchrun): every rank runs its
 own column (independent problems, no collective), value = all ranks' fluid
 updates / the slowest rank's time.
@@ -35,6 +38,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_FLUID_NODE = 152  # 19 populations x 4 B, read + write
+BYTES_PER_LINK = 8  # one population read, the bounced value written
 METRIC = "coupled step MLUPS (fluid nodes)"
 UNIT = "MLUPS"
 
@@ -106,25 +110,28 @@ class Clocks:
 
 
 def _kernel_hash():
+    """Hash of the CUDA sources: a profile is valid only for the code it measured."""
+    import glob
     h = hashlib.sha256()
-    for f in ("lattice.cu", "common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1808_08921_gb300", "csrc", f), "rb").read())
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1808_08921_gb300", "csrc", "*.cu*"))):
+        h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic():
-    """DRAM bytes per collide+stream launch from the committed ncu summary, if
-    it was taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "coupled_step_fcc128x128x1024.md")
-    if not os.path.exists(p):
+PROFILE = os.path.join(ROOT, "profiles", "coupled_step_fcc128x128x1024.md")
+
+
+def _profiled_traffic(group):
+    """DRAM bytes per launch of a kernel group from the committed ncu summary,
+    if it was taken on the current kernel sources (else None)."""
+    if not os.path.exists(PROFILE):
         return None
-    txt = open(p).read()
-    kh = None
-    val = None
-    for line in txt.splitlines():
+    kh, val = None, None
+    key = f"dram_bytes_per_launch[{group}]:"
+    for line in open(PROFILE).read().splitlines():
         if line.startswith("kernel_source_hash:"):
             kh = line.split(":", 1)[1].strip()
-        if line.startswith("dram_bytes_per_launch_full_size:"):
+        if line.startswith(key):
             try:
                 val = float(line.split(":", 1)[1].strip())
             except ValueError:
@@ -185,12 +192,29 @@ def run_ours(args):
     else:
         ms_max, fluid_sum = ms, float(fluid)
     value = fluid_sum * args.steps / (ms_max * 1e-3) / 1e6
-    # roofline of the dominant kernel (collide+stream, both parities)
-    k1_ms, k1_n = tm["collide_stream"]
-    k1_avg = k1_ms / max(k1_n, 1)
+    # rooflines of the HBM-bound kernel groups at their algorithmic bytes
+    # (collide+stream: 152 B per fluid node; links: 8 B per link record, the
+    # population read and the bounced value written); the dominant one by
+    # measured time is the headline `roofline`
     peak, peak_kind = _peaks()
-    achieved = BYTES_PER_FLUID_NODE * fluid / (k1_avg * 1e-3) / 1e9
-    traffic = _profiled_traffic()
+    algo = {"collide_stream": (BYTES_PER_FLUID_NODE, fluid, "fluid node"),
+            "links": (BYTES_PER_LINK, cnt_b["links"], "link record")}
+    kernels = {}
+    for g, (per, units, uname) in algo.items():
+        k_ms, k_n = tm[g]
+        avg = k_ms / max(k_n, 1)
+        ach = per * units / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+        kernels[g] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                      "frac": round(ach / peak, 4), "traffic": _profiled_traffic(g),
+                      "bytes_per_launch": per * units, "bytes_per_unit": per, "units": units,
+                      "work_unit": uname, "us_per_launch": round(1e3 * avg, 2), "peak_kind": peak_kind}
+    dom = max(kernels, key=lambda g: kernels[g]["us_per_launch"])
+    roofline = dict(kernels[dom], kernel=dom)
+    step_bytes = BYTES_PER_FLUID_NODE * fluid_sum
+    step_ach = step_bytes * args.steps / (ms_max * 1e-3) / 1e9
+    step_roofline = {"bytes_per_step": step_bytes, "achieved": round(step_ach, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(step_ach / peak, 4),
+                     "note": "whole coupled step at 152 B per fluid node (all kernels in the time)"}
     # end to end through the C ABI from host buffers
     e2e = None
     if not args.no_e2e:
@@ -231,11 +255,9 @@ def run_ours(args):
                        "l2": "inputs larger than L2: populations %.0f MB" % (19 * 4 * cnt_b["stored"] / 1e6),
                        "relayouts_in_timed_region": cnt_b["relayouts"] - cnt_a["relayouts"],
                        "status": st},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": "collide_stream (even+odd AA)", "peak_kind": peak_kind,
-                         "bytes_per_launch": BYTES_PER_FLUID_NODE * fluid,
-                         "us_per_launch": round(1e3 * k1_avg, 2)},
+            "roofline": roofline,
+            "step_roofline": step_roofline,
+            "kernel_rooflines": kernels,
             "kernel_groups": groups,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -184,10 +184,11 @@ int lbm_dem_read_probe(lbmdem_ctx* c, double* trace, int64_t max_len, int64_t* l
 int lbm_dem_read_monitors(lbmdem_ctx* c, double out[6]);
 
 /* Counters of the current layout: out[0] lattice nodes, [1] stored nodes,
- * [2] fluid nodes now, [3] surface nodes tracked for conversion, [4] link
- * candidate nodes, [5] neighbour-list entries, [6] time step t, [7]
- * re-layouts done, [8] node conversions so far, [9] kernels launched by
- * lbm_dem_step so far.  Synchronises. */
+ * [2] fluid nodes now, [3] surface nodes tracked for conversion, [4] fluid-
+ * solid link records (links fixed until the next re-layout plus the links
+ * whose solid end is re-decided every step), [5] neighbour-list entries,
+ * [6] time step t, [7] re-layouts done, [8] node conversions so far, [9]
+ * kernels launched by lbm_dem_step so far.  Synchronises. */
 int lbm_dem_read_counters(lbmdem_ctx* c, int64_t out[10]);
 
 /* Per-kernel timing with CUDA events on the context stream.  enable = 1

@@ -92,8 +92,10 @@ struct lbmdem_ctx {
     uint32_t nband = 0;
     DBuf<uint32_t> surf_count, surf_off;
     DBuf<uint2> surf_link;
-    DBuf<uint32_t> warp_pd;
+    DBuf<uint32_t> warp_p;
+    DBuf<uint32_t> warp_dirs;  // 4 chunk directions per warp
     uint32_t nwarps = 0;
+    uint32_t nlink_raw = 0;  // link records before padding
     DBuf<Flip> flip_rec;
     DBuf<float> flip_scratch;
     DBuf<uint8_t> flip_valid;
@@ -437,12 +439,12 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
                 c->band_coord.p, c->band_cand.p, nband, &c->st.p->status, c->band.p, nx, ny, nz};
     launch_band_cand(BC, s);
     CK(cudaGetLastError());
-    // link lists, grouped by (sphere, direction)
+    // link lists, grouped by sphere (direction-major inside a sphere)
     int np = c->np;
     size_t ng = (size_t)std::max(np, 1) * (Q - 1);
-    CK(c->surf_count.ensure(ng + 1));
+    CK(c->surf_count.ensure(ng + 2));  // + the total before padding
     CK(c->surf_off.ensure(ng + 1));
-    CK(cudaMemsetAsync(c->surf_count.p, 0, sizeof(uint32_t) * (ng + 1), s));
+    CK(cudaMemsetAsync(c->surf_count.p, 0, sizeof(uint32_t) * (ng + 2), s));
     SurfArgs SA{};
     SA.L = make_lat(c);
     SA.X = c->Xref.p;
@@ -452,15 +454,19 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
     SA.owner = c->owner.p;
     SA.band = c->band.p;
     SA.count = c->surf_count.p;
+    SA.nlink = c->surf_count.p + ng + 1;
     launch_surf_count(SA, np, s);
     exclusive_scan(c->surf_count.p, c->surf_off.p, ng + 1, c->scan_tmp.p, s);
     uint32_t nlink = 0;
     if (int r = read_u32(c, c->surf_off.p + ng, &nlink)) return r;
+    if (int r = read_u32(c, c->surf_count.p + ng + 1, &c->nlink_raw)) return r;
     CK(c->surf_link.ensure(std::max<uint32_t>(nlink, 32)));
-    CK(c->warp_pd.ensure(std::max<uint32_t>(nlink / LINK_WARP, 1)));
+    CK(c->warp_p.ensure(std::max<uint32_t>(nlink / LINK_WARP, 1)));
+    CK(c->warp_dirs.ensure(std::max<uint32_t>(nlink / LINK_WARP, 1)));
     SA.offset = c->surf_off.p;
     SA.link = c->surf_link.p;
-    SA.warp_pd = c->warp_pd.p;
+    SA.warp_p = c->warp_p.p;
+    SA.chunk_dir = reinterpret_cast<uint8_t*>(c->warp_dirs.p);
     launch_surf_fill(SA, np, s);
     CK(cudaGetLastError());
     c->nwarps = nlink / LINK_WARP;
@@ -562,7 +568,7 @@ static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
         if (tm) record_pair_begin(c, 0, e);
         launch_collide(L, mon, parity == 1, monitor, s);
         if (tm) record_pair_end(c, e);
-        LinkLists LL{c->surf_link.p, c->warp_pd.p, c->nwarps};
+        LinkLists LL{c->surf_link.p, c->warp_p.p, c->warp_dirs.p, c->nwarps};
         if (tm) record_pair_begin(c, 1, e);
         launch_links(L, P, LL, s);
         if (tm) record_pair_end(c, e);
@@ -1152,7 +1158,7 @@ int lbm_dem_read_counters(lbmdem_ctx* c, int64_t out[10]) {
     out[1] = c->nS;
     out[2] = fluid;
     out[3] = c->nband;
-    out[4] = (int64_t)c->nwarps * LINK_WARP;
+    out[4] = (int64_t)c->nlink_raw;
     out[5] = nb;
     out[6] = c->t;
     out[7] = c->relayouts;

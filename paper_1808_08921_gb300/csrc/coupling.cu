@@ -1,7 +1,7 @@
 // coupling.cu -- fluid-solid coupling (Section 2.3).
 //
-//  * k_links: walks each sphere's link lists (one warp per 32 links of one
-//    sphere in one direction).  For every fluid node x and direction d whose
+//  * k_links: walks each sphere's link lists (one warp per LINK_WARP links of
+//    one sphere, in chunks of 32 links of one direction).  For every fluid node x and direction d whose
 //    neighbour x + c_d belongs to the sphere, slot opp(d) of x holds the
 //    post-collision value f~_d(x) (AA layout, either parity); it is replaced
 //    by the bounced value f~_d - 6 w_d rho_f c_d . V_b (Eq. 14, moving wall
@@ -76,69 +76,108 @@ struct Dir {
     }
 };
 
-// LINK_WARP / 32 links per thread, all of sphere p in direction d.  The
-// phases (records, fluid bits, ownership, populations, updates) each issue
-// all of the thread's loads before using any, so the K chains overlap.
-__device__ __noinline__ void link_warp(const Lat& L, const PartView& P, const LinkLists& B, uint32_t w, int p,
-                                       const Dir& d, float* acc) {
+// The same directions as a constant table, read with a warp-uniform index.
+struct DirC {
+    float cx, cy, cz, w;
+    int op;
+};
+__constant__ DirC kDir[Q - 1] = {
+#define LBMDEM_DIR(m) {(float)cx(m), (float)cy(m), (float)cz(m), wt(m), opp(m)}
+    LBMDEM_DIR(0),  LBMDEM_DIR(1),  LBMDEM_DIR(2),  LBMDEM_DIR(3),  LBMDEM_DIR(4),  LBMDEM_DIR(5),
+    LBMDEM_DIR(6),  LBMDEM_DIR(7),  LBMDEM_DIR(8),  LBMDEM_DIR(9),  LBMDEM_DIR(10), LBMDEM_DIR(11),
+    LBMDEM_DIR(12), LBMDEM_DIR(13), LBMDEM_DIR(14), LBMDEM_DIR(15), LBMDEM_DIR(16), LBMDEM_DIR(17),
+#undef LBMDEM_DIR
+};
+
+static_assert(LINK_WARP == 4 * 32, "the warp table holds four chunk directions");
+
+// b - 128 for the byte b at bit `shift` of a record word, exactly, as FP32
+// (2^23 + b from the bits, minus 2^23 + 128: no conversion instruction).
+__device__ __forceinline__ float rel_f(uint32_t word, int shift) {
+    return __uint_as_float(0x4B000000u | ((word >> shift) & 255u)) - 8388736.0f;
+}
+
+// Does sphere p own the band neighbour x + c_m of the link node now?
+// Decided by the map update's FP32 test (same operands and rounding) away
+// from its margin, else (or when several spheres may claim the node) by
+// the owner map.
+__device__ __forceinline__ bool owns_neighbour(const Lat& L, const PartView& P, int p, uint32_t y, int m,
+                                               const float4& xf, float R2) {
+    const Dir d(m);
+    if (!(y >> 25 & 1u)) {
+        float ax = __fsub_rn(rel_f(y, 0) + (float)d.cx, xf.x), ay = __fsub_rn(rel_f(y, 8) + (float)d.cy, xf.y),
+              az = __fsub_rn(rel_f(y, 16) + (float)d.cz, xf.z);
+        float d2 = norm2_rn(ax, ay, az);
+        if (fabsf(d2 - R2) > FP32_MARGIN * R2) return d2 < R2;
+    }
+    int ix = (int)(y & 255u) - 128, iy = (int)((y >> 8) & 255u) - 128, iz = (int)((y >> 16) & 255u) - 128;
+    int4 o = P.orgw[p];  // wrapped origin: the offsets are small
+    int xs = o.x + ix + d.cx, ys = o.y + iy + d.cy, zs = o.z + iz + d.cz;
+    if (L.px) xs = xs < 0 ? xs + L.nx : (xs >= L.nx ? xs - L.nx : xs);
+    ys = ys < 0 ? ys + L.ny : (ys >= L.ny ? ys - L.ny : ys);
+    zs = zs < 0 ? zs + L.nz : (zs >= L.nz ? zs - L.nz : zs);
+    return L.owner[((size_t)xs * L.ny + ys) * L.nz + zs] == p;
+}
+
+// One warp: LINK_WARP links of one sphere in four chunks of 32, each chunk in
+// one direction.  The phases (records, fluid bits, ownership, populations,
+// updates) each issue all of the thread's loads before using any.  With c
+// uniform over a chunk, the moving-wall term of Eq. 14 is
+// 6 w rho_f c.(V + W x b) = alpha + r.beta with alpha = 6 w rho_f c.V and
+// beta = 6 w rho_f (c x W) (b = r + c/2 and c.(W x c) = 0).  Warp-shuffle
+// sums, then one FP64 atomic per component per warp into one of NREP
+// accumulator copies of the sphere.
+__global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
     constexpr int K = LINK_WARP / 32;
+    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= B.nwarps) return;  // whole warps
     const uint32_t lane = threadIdx.x & 31;
+    const int p = (int)B.warp_p[w];
+    const uint32_t dirs = B.warp_dirs[w];
     const uint2* rec = B.link + (size_t)w * LINK_WARP + lane;
     uint2 lk[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) lk[k] = __ldcs(&rec[k * 32]);
-    uint32_t fb[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) fb[k] = lk[k].x != NONE ? __ldg(&L.fbits[lk[k].x >> 5]) : 0u;
-    float4 xf = P.xf[p];
-    float4 V = P.V[p], W = P.W[p];
-    const float R2 = __fmul_rn(P.R[p], P.R[p]);
+    const float4 xf = P.xf[p];
+    const float4 V = P.V[p], W = P.W[p];
     bool on[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        on[k] = lk[k].x != NONE && ((fb[k] >> (lk[k].x & 31)) & 1u);
-        if (on[k] && (lk[k].y >> 24 & 1u)) {  // band neighbour: does the sphere own it now?
-            int ix = (int)(lk[k].y & 255u) - 128, iy = (int)((lk[k].y >> 8) & 255u) - 128,
-                iz = (int)((lk[k].y >> 16) & 255u) - 128;
-            bool read_owner = (lk[k].y >> 25 & 1u) != 0;  // another sphere may claim it
-            if (!read_owner) {
-                // the map update's FP32 test, same operands and rounding
-                float ax = __fsub_rn((float)(ix + d.cx), xf.x), ay = __fsub_rn((float)(iy + d.cy), xf.y),
-                      az = __fsub_rn((float)(iz + d.cz), xf.z);
-                float d2 = norm2_rn(ax, ay, az);
-                if (fabsf(d2 - R2) <= FP32_MARGIN * R2)
-                    read_owner = true;
-                else
-                    on[k] = d2 < R2;
-            }
-            if (read_owner) {
-                int4 o = P.orgw[p];  // wrapped origin: the offsets are small
-                int xs = o.x + ix + d.cx, ys = o.y + iy + d.cy, zs = o.z + iz + d.cz;
-                if (L.px) xs = xs < 0 ? xs + L.nx : (xs >= L.nx ? xs - L.nx : xs);
-                ys = ys < 0 ? ys + L.ny : (ys >= L.ny ? ys - L.ny : ys);
-                zs = zs < 0 ? zs + L.nz : (zs >= L.nz ? zs - L.nz : zs);
-                on[k] = L.owner[((size_t)xs * L.ny + ys) * L.nz + zs] == p;
-            }
+    for (int k = 0; k < K; ++k) on[k] = lk[k].x != NONE;
+    if (dirs & 0x80808080u) {  // some chunk holds flagged links
+        uint32_t fb[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k)  // only a node inside a band can have been covered
+            fb[k] = on[k] && (lk[k].y >> 26 & 1u) ? __ldg(&L.fbits[lk[k].x >> 5]) : ~0u;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            on[k] = on[k] && ((fb[k] >> (lk[k].x & 31)) & 1u);
+            if (on[k] && (lk[k].y >> 24 & 1u))
+                on[k] = owns_neighbour(L, P, p, lk[k].y, (int)((dirs >> (8 * k)) & 31u), xf,
+                                       __fmul_rn(P.R[p], P.R[p]));
         }
     }
-    float* plane = L.f + (size_t)d.op * L.nSpad;
     float v[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = on[k] ? plane[lk[k].x] : 0.f;
-    const float c6w = 6.0f * L.rho_f * d.w;
+    for (int k = 0; k < K; ++k) {
+        const int op = kDir[(dirs >> (8 * k)) & 31u].op;
+        v[k] = on[k] ? L.f[(size_t)op * L.nSpad + lk[k].x] : 0.f;
+    }
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float s6 = 6.0f * L.rho_f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+        const DirC d = kDir[(dirs >> (8 * k)) & 31u];
+        const float sw = s6 * d.w;
+        const float alpha = sw * (d.cx * V.x + d.cy * V.y + d.cz * V.z);
+        const float bx = sw * (d.cy * W.z - d.cz * W.y), by = sw * (d.cz * W.x - d.cx * W.z),
+                    bz = sw * (d.cx * W.y - d.cy * W.x);
         if (!on[k]) continue;
-        int ix = (int)(lk[k].y & 255u) - 128, iy = (int)((lk[k].y >> 8) & 255u) - 128,
-            iz = (int)((lk[k].y >> 16) & 255u) - 128;
-        float rx = (float)ix - xf.x, ry = (float)iy - xf.y, rz = (float)iz - xf.z;
-        float bx = rx + 0.5f * d.cx, by = ry + 0.5f * d.cy, bz = rz + 0.5f * d.cz;
-        float cv = d.cx * (V.x + (W.y * bz - W.z * by)) + d.cy * (V.y + (W.z * bx - W.x * bz)) +
-                   d.cz * (V.z + (W.x * by - W.y * bx));
-        float delta = c6w * cv;
-        plane[lk[k].x] = v[k] - delta;
-        float q = 2.0f * v[k] - delta;
-        float qx = d.cx * q, qy = d.cy * q, qz = d.cz * q;
+        const uint32_t y = lk[k].y;
+        const float rx = rel_f(y, 0) - xf.x, ry = rel_f(y, 8) - xf.y, rz = rel_f(y, 16) - xf.z;
+        const float delta = alpha + (rx * bx + ry * by + rz * bz);
+        L.f[(size_t)d.op * L.nSpad + lk[k].x] = v[k] - delta;
+        const float q = 2.0f * v[k] - delta;
+        const float qx = d.cx * q, qy = d.cy * q, qz = d.cz * q;
         acc[0] += qx;
         acc[1] += qy;
         acc[2] += qz;
@@ -147,25 +186,12 @@ __device__ __noinline__ void link_warp(const Lat& L, const PartView& P, const Li
         acc[4] += rz * qx - rx * qz;
         acc[5] += rx * qy - ry * qx;
     }
-}
-
-// One warp: LINK_WARP links of one sphere in one direction (no divergence
-// between lanes); warp-shuffle sums, then one FP64 atomic per component per
-// warp into one of NREP accumulator copies of the sphere.
-__global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
-    uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w >= B.nwarps) return;  // whole warps
-    uint32_t pd = B.warp_pd[w];
-    int p = (int)(pd >> 5);
-    Dir d((int)(pd & 31u));
-    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    link_warp(L, P, B, w, p, d, acc);
     const unsigned full = 0xffffffffu;
 #pragma unroll
     for (int o = 16; o; o >>= 1)
 #pragma unroll
         for (int c = 0; c < 6; ++c) acc[c] += __shfl_xor_sync(full, acc[c], o);
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         size_t rep = (size_t)(w % NREP) * P.n + p;
         double* F = P.Fh + 3 * rep;
         double* T = P.Th + 3 * rep;
@@ -299,105 +325,104 @@ __global__ void k_map_band(MapArgs A) {
     }
 }
 
-// One warp per queued node: lanes 0..18 gather the node (lane 18, c = 0)
-// and its 18 neighbours with the old map; lane 0 applies the conversion.
-__device__ void map_gather_convert_one(const MapArgs& A, uint32_t w, int lane) {
+// One block per queued node (grid-stride over the queue): thread t < 361
+// gathers population m = t % 19 of node j = t / 19 with the old map, where
+// j < 18 is the neighbour x + c_j and j = 18 the node itself; the block's
+// first thread then applies the conversion.
+constexpr int MAP_THREADS = 384;  // >= 19 * 19
+__global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
     const Lat& L = A.L;
-    Flip f = A.F.rec[w];
-    int x, y, z;
-    unpack_coord(f.coord, x, y, z);
-    float* sc = A.F.scratch + (size_t)w * Q * Q;
-    bool valid = false;
-    float rho_j = 0.f;
-    if (lane < Q) {
-        int xs = x + cx(lane), ys = wrap1(y + cy(lane), L.ny), zs = wrap1(z + cz(lane), L.nz);
-        bool in = true;
-        if (L.px) xs = wrap1(xs, L.nx);
-        else in = xs >= 0 && xs < L.nx;
-        if (in) {
-            bool fl;
-            uint32_t ci = stored_index(L, xs, ys, zs, fl);
-            if (fl && ci != NONE) {
-                float s = 0.f;
-#pragma unroll
-                for (int m = 0; m < Q; ++m) {
-                    float g = *pop_loc(L, A.after_even, xs, ys, zs, ci, m);
-                    sc[lane * Q + m] = g;
-                    s += g;
+    __shared__ float sg[Q * Q];
+    __shared__ int sv[Q];
+    const uint32_t nf = min(A.st->nflip[A.par], A.F.cap);
+    const int t = threadIdx.x, j = t / Q, m = t % Q;
+    for (uint32_t w = blockIdx.x; w < nf; w += gridDim.x) {
+        const Flip f = A.F.rec[w];
+        int x, y, z;
+        unpack_coord(f.coord, x, y, z);
+        float* sc = A.F.scratch + (size_t)w * Q * Q;
+        if (t < Q * Q) {
+            bool valid = false;
+            float g = 0.f;
+            int xs = x + cx(j), ys = wrap1(y + cy(j), L.ny), zs = wrap1(z + cz(j), L.nz);
+            bool in = true;
+            if (L.px) xs = wrap1(xs, L.nx);
+            else in = xs >= 0 && xs < L.nx;
+            if (in) {
+                bool fl;
+                uint32_t ci = stored_index(L, xs, ys, zs, fl);
+                if (fl && ci != NONE) {
+                    g = *pop_loc(L, A.after_even, xs, ys, zs, ci, m);
+                    valid = true;
                 }
-                rho_j = L.rho_f + s;
-                valid = true;
+            }
+            sg[t] = g;
+            if (valid) sc[t] = g;
+            if (m == 0) sv[j] = valid ? 1 : 0;
+        }
+        __syncthreads();
+        if (t == 0) {
+            // mean density of the fluid neighbours (not the node itself)
+            float rs = 0.f, rc = 0.f;
+            for (int jj = 0; jj < Q - 1; ++jj) {
+                if (!sv[jj]) continue;
+                float d = 0.f;
+                for (int mm = 0; mm < Q; ++mm) d += sg[jj * Q + mm];
+                rs += L.rho_f + d;
+                rc += 1.f;
+            }
+            int o = f.old_owner, nw = f.new_owner;
+            if (o == OWNER_FLUID && nw != OWNER_FLUID) {
+                // covered: the sphere gains the node's momentum (Eq. 16)
+                const float* g = sg + 18 * Q;
+                double jm[3] = {0, 0, 0};
+                for (int mm = 0; mm < Q; ++mm) {
+                    jm[0] += cx(mm) * (double)g[mm];
+                    jm[1] += cy(mm) * (double)g[mm];
+                    jm[2] += cz(mm) * (double)g[mm];
+                }
+                double X0, X1, X2;
+                centre(A.P, nw, X0, X1, X2);
+                double r[3] = {node_offset(x, X0, L.nx, L.px), node_offset(y, X1, L.ny, 1),
+                               node_offset(z, X2, L.nz, 1)};
+                atomicAdd(&A.P.Fh[3 * nw], jm[0]);
+                atomicAdd(&A.P.Fh[3 * nw + 1], jm[1]);
+                atomicAdd(&A.P.Fh[3 * nw + 2], jm[2]);
+                atomicAdd(&A.P.Th[3 * nw], r[1] * jm[2] - r[2] * jm[1]);
+                atomicAdd(&A.P.Th[3 * nw + 1], r[2] * jm[0] - r[0] * jm[2]);
+                atomicAdd(&A.P.Th[3 * nw + 2], r[0] * jm[1] - r[1] * jm[0]);
+            } else if (o != OWNER_FLUID && nw == OWNER_FLUID) {
+                // uncovered: equilibrium at rho_bar and the surface velocity (Eq. 17)
+                double rb = rc > 0.f ? (double)rs / (double)rc : (double)L.rho_f;
+                double X0, X1, X2;
+                centre(A.P, o, X0, X1, X2);
+                double r[3] = {node_offset(x, X0, L.nx, L.px), node_offset(y, X1, L.ny, 1),
+                               node_offset(z, X2, L.nz, 1)};
+                float4 V = A.P.V[o], W = A.P.W[o];
+                double vb[3] = {V.x + (W.y * r[2] - W.z * r[1]), V.y + (W.z * r[0] - W.x * r[2]),
+                                V.z + (W.x * r[1] - W.y * r[0])};
+                float rbf = (float)rb;
+                float ux = (float)vb[0], uy = (float)vb[1], uz = (float)vb[2];
+                float uu15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+                float* g = sc + 18 * Q;
+                for (int mm = 0; mm < Q; ++mm) {
+                    float cu = cx(mm) * ux + cy(mm) * uy + cz(mm) * uz;
+                    g[mm] = wt(mm) * ((rbf - L.rho_f) + rbf * (3.f * cu + 4.5f * cu * cu - uu15));
+                }
+                sv[18] = 1;
+                double mom[3] = {rb * vb[0], rb * vb[1], rb * vb[2]};
+                atomicAdd(&A.P.Fh[3 * o], -mom[0]);
+                atomicAdd(&A.P.Fh[3 * o + 1], -mom[1]);
+                atomicAdd(&A.P.Fh[3 * o + 2], -mom[2]);
+                atomicAdd(&A.P.Th[3 * o], -(r[1] * mom[2] - r[2] * mom[1]));
+                atomicAdd(&A.P.Th[3 * o + 1], -(r[2] * mom[0] - r[0] * mom[2]));
+                atomicAdd(&A.P.Th[3 * o + 2], -(r[0] * mom[1] - r[1] * mom[0]));
             }
         }
+        __syncthreads();
+        if (t < Q) A.F.valid[(size_t)w * Q + t] = (uint8_t)sv[t];
+        __syncthreads();  // shared arrays are reused by the next queued node
     }
-    const unsigned full = 0xffffffffu;
-    // mean density of the fluid neighbours (not the node itself)
-    float rs = (lane < Q - 1 && valid) ? rho_j : 0.f;
-    float rc = (lane < Q - 1 && valid) ? 1.f : 0.f;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        rs += __shfl_xor_sync(full, rs, o);
-        rc += __shfl_xor_sync(full, rc, o);
-    }
-    __syncwarp();
-    if (lane < Q) A.F.valid[(size_t)w * Q + lane] = valid ? 1 : 0;
-    __syncwarp();  // lane 0 may set the node's own flag below
-    if (lane != 0) return;
-    int o = f.old_owner, nw = f.new_owner;
-    if (o == OWNER_FLUID && nw != OWNER_FLUID) {
-        // covered: the sphere gains the node's momentum (Eq. 16)
-        const float* g = sc + 18 * Q;
-        double j[3] = {0, 0, 0};
-        for (int m = 0; m < Q; ++m) {
-            j[0] += cx(m) * (double)g[m];
-            j[1] += cy(m) * (double)g[m];
-            j[2] += cz(m) * (double)g[m];
-        }
-        double X0, X1, X2;
-        centre(A.P, nw, X0, X1, X2);
-        double r[3] = {node_offset(x, X0, L.nx, L.px), node_offset(y, X1, L.ny, 1),
-                       node_offset(z, X2, L.nz, 1)};
-        atomicAdd(&A.P.Fh[3 * nw], j[0]);
-        atomicAdd(&A.P.Fh[3 * nw + 1], j[1]);
-        atomicAdd(&A.P.Fh[3 * nw + 2], j[2]);
-        atomicAdd(&A.P.Th[3 * nw], r[1] * j[2] - r[2] * j[1]);
-        atomicAdd(&A.P.Th[3 * nw + 1], r[2] * j[0] - r[0] * j[2]);
-        atomicAdd(&A.P.Th[3 * nw + 2], r[0] * j[1] - r[1] * j[0]);
-    } else if (o != OWNER_FLUID && nw == OWNER_FLUID) {
-        // uncovered: equilibrium at rho_bar and the surface velocity (Eq. 17)
-        double rb = rc > 0.f ? (double)rs / (double)rc : (double)L.rho_f;
-        double X0, X1, X2;
-        centre(A.P, o, X0, X1, X2);
-        double r[3] = {node_offset(x, X0, L.nx, L.px), node_offset(y, X1, L.ny, 1),
-                       node_offset(z, X2, L.nz, 1)};
-        float4 V = A.P.V[o], W = A.P.W[o];
-        double vb[3] = {V.x + (W.y * r[2] - W.z * r[1]), V.y + (W.z * r[0] - W.x * r[2]),
-                        V.z + (W.x * r[1] - W.y * r[0])};
-        float rbf = (float)rb;
-        float ux = (float)vb[0], uy = (float)vb[1], uz = (float)vb[2];
-        float uu15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-        float* g = sc + 18 * Q;
-        for (int m = 0; m < Q; ++m) {
-            float cu = cx(m) * ux + cy(m) * uy + cz(m) * uz;
-            g[m] = wt(m) * ((rbf - L.rho_f) + rbf * (3.f * cu + 4.5f * cu * cu - uu15));
-        }
-        A.F.valid[(size_t)w * Q + 18] = 1;
-        double mom[3] = {rb * vb[0], rb * vb[1], rb * vb[2]};
-        atomicAdd(&A.P.Fh[3 * o], -mom[0]);
-        atomicAdd(&A.P.Fh[3 * o + 1], -mom[1]);
-        atomicAdd(&A.P.Fh[3 * o + 2], -mom[2]);
-        atomicAdd(&A.P.Th[3 * o], -(r[1] * mom[2] - r[2] * mom[1]));
-        atomicAdd(&A.P.Th[3 * o + 1], -(r[2] * mom[0] - r[0] * mom[2]));
-        atomicAdd(&A.P.Th[3 * o + 2], -(r[0] * mom[1] - r[1] * mom[0]));
-    }
-}
-
-__global__ void k_map_gather_convert(MapArgs A) {
-    int lane = threadIdx.x & 31;
-    uint32_t nf = min(A.st->nflip[A.par], A.F.cap);
-    uint32_t nwarp = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nf; w += nwarp)
-        map_gather_convert_one(A, w, lane);
 }
 
 __device__ void map_commit_one(const MapArgs& A, uint32_t k);
@@ -433,31 +458,25 @@ __device__ void map_commit_one(const MapArgs& A, uint32_t k) {
     L.owner[li] = f.new_owner;
 }
 
-__device__ void map_scatter_one(const MapArgs& A, uint32_t w, int lane);
-
-__global__ void k_map_scatter(MapArgs A) {
-    int lane = threadIdx.x & 31;
-    uint32_t nf = min(A.st->nflip[A.par], A.F.cap);
-    uint32_t nwarp = (gridDim.x * blockDim.x) >> 5;
-    if (lane >= Q) return;
-    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nf; w += nwarp)
-        map_scatter_one(A, w, lane);
-}
-
-__device__ void map_scatter_one(const MapArgs& A, uint32_t w, int lane) {
-    if (!A.F.valid[(size_t)w * Q + lane]) return;
-    const Lat& L = A.L;
-    Flip f = A.F.rec[w];
-    int x, y, z;
-    unpack_coord(f.coord, x, y, z);
-    int xs = x + cx(lane), ys = wrap1(y + cy(lane), L.ny), zs = wrap1(z + cz(lane), L.nz);
-    if (L.px) xs = wrap1(xs, L.nx);
-    bool fl;
-    uint32_t ci = stored_index(L, xs, ys, zs, fl);
-    if (!fl || ci == NONE) return;
-    const float* sc = A.F.scratch + (size_t)w * Q * Q + lane * Q;
-#pragma unroll
-    for (int m = 0; m < Q; ++m) *pop_loc(L, A.after_even, xs, ys, zs, ci, m) = sc[m];
+// One block per queued node: thread t < 361 writes population m = t % 19 of
+// node j = t / 19 back with the new map.
+__global__ void __launch_bounds__(MAP_THREADS) k_map_scatter(MapArgs A) {
+    const Lat L = A.L;
+    const uint32_t nf = min(A.st->nflip[A.par], A.F.cap);
+    const int t = threadIdx.x, j = t / Q, m = t % Q;
+    if (t >= Q * Q) return;
+    for (uint32_t w = blockIdx.x; w < nf; w += gridDim.x) {
+        if (!A.F.valid[(size_t)w * Q + j]) continue;
+        const Flip f = A.F.rec[w];
+        int x, y, z;
+        unpack_coord(f.coord, x, y, z);
+        int xs = x + cx(j), ys = wrap1(y + cy(j), L.ny), zs = wrap1(z + cz(j), L.nz);
+        if (L.px) xs = wrap1(xs, L.nx);
+        bool fl;
+        uint32_t ci = stored_index(L, xs, ys, zs, fl);
+        if (!fl || ci == NONE) continue;
+        *pop_loc(L, A.after_even, xs, ys, zs, ci, m) = A.F.scratch[(size_t)w * Q * Q + t];
+    }
 }
 
 void launch_map_update(const Lat& L, const PartView& P, const Band& band, const FlipBuf& F,
@@ -469,9 +488,9 @@ void launch_map_update(const Lat& L, const PartView& P, const Band& band, const 
     if (band.n == 0) return;
     // the queued count is read on the device: fixed grids stride over it
     const unsigned grid = 2 * 152;
-    k_map_gather_convert<<<grid, 256, 0, s>>>(A);
+    k_map_gather_convert<<<grid, MAP_THREADS, 0, s>>>(A);
     k_map_commit<<<grid, 256, 0, s>>>(A);
-    k_map_scatter<<<grid, 256, 0, s>>>(A);
+    k_map_scatter<<<grid, MAP_THREADS, 0, s>>>(A);
 }
 
 }  // namespace lbmdem

@@ -1,7 +1,12 @@
 // dem.cu -- the solid phase (Section 2.2, Eqs. 9-12).
 //
-//  * k_dem_step: one launch per LBM step, one thread-block cluster (<= 8
-//    CTAs, co-scheduled), one thread per sphere.  It runs the K velocity-
+//  * k_dem_step_dsm: one launch per LBM step, one thread-block cluster of up
+//    to 16 CTAs, a team of TEAM threads per sphere holding the sphere's
+//    state in registers; positions and half-step velocities are exchanged
+//    through distributed shared memory.  k_dem_step is the general form
+//    (state in global memory, several spheres per team) for packings too
+//    large for one cluster, and computes the initial contact forces.
+//  * Both: one thread-block cluster (co-scheduled), a team per sphere.  It runs the K velocity-
 //    Verlet substeps of length 1/K with the hydrodynamic force and torque of
 //    the step held fixed: kick + drift of the own sphere, one cluster barrier,
 //    then the contact forces of the own sphere from its neighbour list and
@@ -40,17 +45,68 @@ __device__ __forceinline__ float3 crossf(float3 a, float3 b) {
 
 constexpr int TEAM = 4;  // threads per sphere: they share its neighbour list
 
-// Contact forces on sphere i (Eqs. 11-12): Hertz normal force, incremental
-// Mindlin tangential force from the half-step relative velocity at the
-// contact point, previous tangential force projected on the current tangent
-// plane, Coulomb cap.  dt_inc = 0 evaluates without tangential increment.
-// Lane `tl` of the sphere's team takes entries tl, tl + TEAM, ...; the
-// caller reduces over the team.
+// One contact of sphere i with neighbour entry (j, image) (Eqs. 11-12):
+// Hertz normal force, incremental Mindlin tangential force from the
+// half-step relative velocity at the contact point, previous tangential
+// force projected on the current tangent plane, Coulomb cap.  dl = dX_j -
+// dX_i; dr = the entry's reference separation (w: (R_i + R_j)^2 - |xyz|^2).
+// Updates the history h (force on i) and adds the force and torque on i.
+// The arithmetic is mirror-exact: sphere j, evaluating the same pair,
+// obtains exactly the negative force.
+__device__ __forceinline__ void pair_contact(const Dem& D, float Ri, float Rj, float3 dl, float4 dr, float3 vi,
+                                             float3 wi, float3 vj, float3 wj, float dt_inc, float4& h, float3& F,
+                                             float3& T) {
+    float3 d = make_float3(dr.x + dl.x, dr.y + dl.y, dr.z + dl.z);
+    float cut = Ri + Rj;
+    // cut^2 - |d|^2 without cancellation: e0 - 2 dref.dl - dl.dl
+    float qd = dr.w - (2.f * (dr.x * dl.x + dr.y * dl.y + dr.z * dl.z) + (dl.x * dl.x + dl.y * dl.y + dl.z * dl.z));
+    if (!(qd > 0.f)) {
+        h = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    float dist = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+    float delta = qd / (cut + dist);
+    float3 n = make_float3(d.x / dist, d.y / dist, d.z / dist);
+    float Rs = Ri * Rj / (Ri + Rj);
+    float sq = sqrtf(Rs * delta);
+    float fn = D.kn * sq * delta;
+    float ai = Ri - 0.5f * delta, aj = Rj - 0.5f * delta;
+    float3 ri = make_float3(ai * n.x, ai * n.y, ai * n.z);
+    float3 rj = make_float3(-(aj * n.x), -(aj * n.y), -(aj * n.z));
+    float3 cwj = crossf(wj, rj), cwi = crossf(wi, ri);
+    float3 vr = make_float3((vj.x + cwj.x) - (vi.x + cwi.x), (vj.y + cwj.y) - (vi.y + cwi.y),
+                            (vj.z + cwj.z) - (vi.z + cwi.z));
+    float vn = vr.x * n.x + vr.y * n.y + vr.z * n.z;
+    float3 vt = make_float3(vr.x - vn * n.x, vr.y - vn * n.y, vr.z - vn * n.z);
+    float hn = h.x * n.x + h.y * n.y + h.z * n.z;
+    float kdt = D.kt * sq * dt_inc;
+    float3 ft = make_float3(h.x - hn * n.x + kdt * vt.x, h.y - hn * n.y + kdt * vt.y, h.z - hn * n.z + kdt * vt.z);
+    float ftm = sqrtf(ft.x * ft.x + ft.y * ft.y + ft.z * ft.z);
+    float cap = D.mu * fn;
+    if (ftm > cap) {
+        float sc = cap / ftm;
+        ft = make_float3(ft.x * sc, ft.y * sc, ft.z * sc);
+    }
+    h = make_float4(ft.x, ft.y, ft.z, 0.f);
+    float3 Fk = make_float3(-fn * n.x + ft.x, -fn * n.y + ft.y, -fn * n.z + ft.z);
+    float3 Tk = crossf(ri, Fk);
+    F.x += Fk.x;
+    F.y += Fk.y;
+    F.z += Fk.z;
+    T.x += Tk.x;
+    T.y += Tk.y;
+    T.z += Tk.z;
+}
+
+// Contact forces on sphere i from its neighbour list, positions and half-
+// step velocities of substep buffer b in global memory.  dt_inc = 0
+// evaluates without tangential increment.  Lane `tl` of the sphere's team
+// takes entries tl, tl + TEAM, ...; the caller reduces over the team.
 __device__ void contact_forces(const Dem& D, int i, int b, float dt_inc, int tl, float3& F, float3& T) {
     F = make_float3(0.f, 0.f, 0.f);
     T = make_float3(0.f, 0.f, 0.f);
-    float4 xi4 = __ldcg(&D.dXb[b * D.n + i]);
-    float3 xi = f3(xi4), vi = f3(__ldcg(&D.Vhb[b * D.n + i])), wi = f3(__ldcg(&D.Whb[b * D.n + i]));
+    float3 xi = f3(__ldcg(&D.dXb[b * D.n + i]));
+    float3 vi = f3(__ldcg(&D.Vhb[b * D.n + i])), wi = f3(__ldcg(&D.Whb[b * D.n + i]));
     float Ri = D.R[i];
     int cnt = D.nb_cnt[i];
     for (int k = tl; k < cnt; k += TEAM) {
@@ -58,53 +114,46 @@ __device__ void contact_forces(const Dem& D, int i, int b, float dt_inc, int tl,
         int j = D.nb_j[e];
         float4 dr = D.nb_dref[e];
         float3 xj = f3(__ldcg(&D.dXb[b * D.n + j]));
-        float3 dl = make_float3(xj.x - xi.x, xj.y - xi.y, xj.z - xi.z);
-        float3 d = make_float3(dr.x + dl.x, dr.y + dl.y, dr.z + dl.z);
-        float Rj = D.R[j];
-        float cut = Ri + Rj;
-        // cut^2 - |d|^2 without cancellation: e0 - 2 dref.dl - dl.dl
-        float qd = dr.w - (2.f * (dr.x * dl.x + dr.y * dl.y + dr.z * dl.z) +
-                           (dl.x * dl.x + dl.y * dl.y + dl.z * dl.z));
-        if (!(qd > 0.f)) {
-            D.nb_ft[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-            continue;
-        }
-        float dist = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-        float delta = qd / (cut + dist);
-        float3 n = make_float3(d.x / dist, d.y / dist, d.z / dist);
-        float Rs = Ri * Rj / (Ri + Rj);
-        float sq = sqrtf(Rs * delta);
-        float fn = D.kn * sq * delta;
-        float ai = Ri - 0.5f * delta, aj = Rj - 0.5f * delta;
-        float3 ri = make_float3(ai * n.x, ai * n.y, ai * n.z);
-        float3 rj = make_float3(-(aj * n.x), -(aj * n.y), -(aj * n.z));
         float3 vj = f3(__ldcg(&D.Vhb[b * D.n + j])), wj = f3(__ldcg(&D.Whb[b * D.n + j]));
-        float3 cwj = crossf(wj, rj), cwi = crossf(wi, ri);
-        float3 vr = make_float3((vj.x + cwj.x) - (vi.x + cwi.x), (vj.y + cwj.y) - (vi.y + cwi.y),
-                                (vj.z + cwj.z) - (vi.z + cwi.z));
-        float vn = vr.x * n.x + vr.y * n.y + vr.z * n.z;
-        float3 vt = make_float3(vr.x - vn * n.x, vr.y - vn * n.y, vr.z - vn * n.z);
         float4 h = D.nb_ft[e];
-        float hn = h.x * n.x + h.y * n.y + h.z * n.z;
-        float kdt = D.kt * sq * dt_inc;
-        float3 ft = make_float3(h.x - hn * n.x + kdt * vt.x, h.y - hn * n.y + kdt * vt.y,
-                                h.z - hn * n.z + kdt * vt.z);
-        float ftm = sqrtf(ft.x * ft.x + ft.y * ft.y + ft.z * ft.z);
-        float cap = D.mu * fn;
-        if (ftm > cap) {
-            float sc = cap / ftm;
-            ft = make_float3(ft.x * sc, ft.y * sc, ft.z * sc);
-        }
-        D.nb_ft[e] = make_float4(ft.x, ft.y, ft.z, 0.f);
-        float3 Fk = make_float3(-fn * n.x + ft.x, -fn * n.y + ft.y, -fn * n.z + ft.z);
-        float3 Tk = crossf(ri, Fk);
-        F.x += Fk.x;
-        F.y += Fk.y;
-        F.z += Fk.z;
-        T.x += Tk.x;
-        T.y += Tk.y;
-        T.z += Tk.z;
+        pair_contact(D, Ri, D.R[j], make_float3(xj.x - xi.x, xj.y - xi.y, xj.z - xi.z), dr, vi, wi, vj, wj,
+                     dt_inc, h, F, T);
+        D.nb_ft[e] = h;
     }
+}
+
+// First half kick of velocity Verlet and the drift of one substep:
+// half-step velocities vh, wh from the contact (fc, tc), hydrodynamic (fa,
+// ta) and body forces; the displacement dx advanced with Kahan-compensated
+// FP32 accumulation (compensation c); q <- normalize(q + dt/2 (0, wh) q).
+__device__ __forceinline__ void kick_drift(const Dem& D, float3 fc, float3 tc, float3 fa, float3 ta, float im,
+                                           float iI, float3 v, float3 w, float3& vh, float3& wh, float3& dx,
+                                           float3& c, float4& q) {
+    const float dt = D.dt;
+    vh = make_float3(v.x + 0.5f * dt * (fc.x + fa.x + D.g.x) * im, v.y + 0.5f * dt * (fc.y + fa.y + D.g.y) * im,
+                     v.z + 0.5f * dt * (fc.z + fa.z + D.g.z) * im);
+    wh = make_float3(w.x + 0.5f * dt * (tc.x + ta.x) * iI, w.y + 0.5f * dt * (tc.y + ta.y) * iI,
+                     w.z + 0.5f * dt * (tc.z + ta.z) * iI);
+    float yx = dt * vh.x - c.x, yy = dt * vh.y - c.y, yz = dt * vh.z - c.z;
+    float tx = dx.x + yx, ty = dx.y + yy, tz = dx.z + yz;
+    c = make_float3((tx - dx.x) - yx, (ty - dx.y) - yy, (tz - dx.z) - yz);
+    dx = make_float3(tx, ty, tz);
+    float dq0 = -(wh.x * q.y + wh.y * q.z + wh.z * q.w);
+    float3 wxv = crossf(wh, make_float3(q.y, q.z, q.w));
+    float4 dq = make_float4(dq0, q.x * wh.x + wxv.x, q.x * wh.y + wxv.y, q.x * wh.z + wxv.z);
+    q = make_float4(q.x + 0.5f * dt * dq.x, q.y + 0.5f * dt * dq.y, q.z + 0.5f * dt * dq.z, q.w + 0.5f * dt * dq.w);
+    float nq = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    q = make_float4(q.x * nq, q.y * nq, q.z * nq, q.w * nq);
+}
+
+// Second half kick: V = vh + dt/2 (F + fa + g) / m, W likewise.
+__device__ __forceinline__ void close_kick(const Dem& D, float3 vh, float3 wh, float3 F, float3 T, float3 fa,
+                                           float3 ta, float im, float iI, float3& v, float3& w) {
+    const float dt = D.dt;
+    v = make_float3(vh.x + 0.5f * dt * (F.x + fa.x + D.g.x) * im, vh.y + 0.5f * dt * (F.y + fa.y + D.g.y) * im,
+                    vh.z + 0.5f * dt * (F.z + fa.z + D.g.z) * im);
+    w = make_float3(wh.x + 0.5f * dt * (T.x + ta.x) * iI, wh.y + 0.5f * dt * (T.y + ta.y) * iI,
+                    wh.z + 0.5f * dt * (T.z + ta.z) * iI);
 }
 
 // sum over the TEAM lanes of a sphere (lanes of a team are consecutive)
@@ -121,13 +170,52 @@ __device__ __forceinline__ void team_sum(float3& F, float3& T) {
     }
 }
 
+// Lattice frame of sphere i after the step (integer origin, wrapped origin,
+// FP32 offset of the centre) and its displacement / speed for the
+// re-layout decision and the NaN / skin checks.
+__device__ __forceinline__ void sphere_frame(const Dem& D, int i, float& dmax, float& vmax, uint32_t& bad) {
+    float4 dx = D.dX[i], c = D.dXc[i], v = D.V[i];
+    double X0 = D.Xref[3 * i] + (double)dx.x - (double)c.x;
+    double X1 = D.Xref[3 * i + 1] + (double)dx.y - (double)c.y;
+    double X2 = D.Xref[3 * i + 2] + (double)dx.z - (double)c.z;
+    int4 o = make_int4((int)floor(D.Xref[3 * i]), (int)floor(D.Xref[3 * i + 1]), (int)floor(D.Xref[3 * i + 2]), 0);
+    D.org[i] = o;
+    int wx = D.px ? (int)(((long long)o.x % (long long)D.Lx + (long long)D.Lx) % (long long)D.Lx) : o.x;
+    int wy = (int)(((long long)o.y % (long long)D.Ly + (long long)D.Ly) % (long long)D.Ly);
+    int wz = (int)(((long long)o.z % (long long)D.Lz + (long long)D.Lz) % (long long)D.Lz);
+    D.orgw[i] = make_int4(wx, wy, wz, 0);
+    D.xf[i] = make_float4((float)(X0 - o.x), (float)(X1 - o.y), (float)(X2 - o.z), 0.f);
+    float dd = sqrtf(dx.x * dx.x + dx.y * dx.y + dx.z * dx.z);
+    float vv = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+    if (!(dd == dd) || !(vv == vv) || isinf(dd) || isinf(vv)) bad |= ST_UNSTABLE;
+    else if (dd >= D.hard_disp) bad |= ST_SKIN;
+    dmax = fmaxf(dmax, dd);
+    vmax = fmaxf(vmax, vv);
+}
+
+// Warp reduction of the maxima and the status bits, one atomic each per warp
+// (every lane of the warp calls it).
+__device__ __forceinline__ void flush_maxima(const Dem& D, float dmax, float vmax, uint32_t bad) {
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        dmax = fmaxf(dmax, __shfl_xor_sync(full, dmax, o));
+        vmax = fmaxf(vmax, __shfl_xor_sync(full, vmax, o));
+        bad |= __shfl_xor_sync(full, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (dmax > 0.f) atomicMax(D.max_disp_bits, __float_as_uint(dmax));
+        if (vmax > 0.f) atomicMax(D.max_vel_bits, __float_as_uint(vmax));
+        if (bad) atomicOr(D.status, bad);
+    }
+}
+
 __global__ void k_dem_step(Dem D, int init_only) {
     cg::cluster_group cl = cg::this_cluster();
     const int nth = gridDim.x * blockDim.x;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int team = tid / TEAM, tl = tid % TEAM, nteams = nth / TEAM;
     const int iters = (D.n + nteams - 1) / nteams;  // uniform: shuffles stay converged
-    const float dt = D.dt;
     if (init_only) {
         for (int i = tid; i < D.n; i += nth) {
             D.dXb[i] = D.dX[i];
@@ -177,31 +265,17 @@ __global__ void k_dem_step(Dem D, int init_only) {
             if (D.fixed[i]) {
                 vh = wh = make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
-                float4 fc = D.Fc[i], tc = D.Tc[i], v = D.V[i], w = D.W[i];
-                float im = D.invm[i], iI = D.invI[i];
-                float4 fa = D.Fa[i], ta = D.Ta[i];
-                vh = make_float4(v.x + 0.5f * dt * (fc.x + fa.x + D.g.x) * im,
-                                 v.y + 0.5f * dt * (fc.y + fa.y + D.g.y) * im,
-                                 v.z + 0.5f * dt * (fc.z + fa.z + D.g.z) * im, 0.f);
-                wh = make_float4(w.x + 0.5f * dt * (tc.x + ta.x) * iI, w.y + 0.5f * dt * (tc.y + ta.y) * iI,
-                                 w.z + 0.5f * dt * (tc.z + ta.z) * iI, 0.f);
-                // drift with Kahan-compensated FP32 accumulation
-                float4 c = D.dXc[i];
-                float yx = dt * vh.x - c.x, yy = dt * vh.y - c.y, yz = dt * vh.z - c.z;
-                float tx = dx.x + yx, ty = dx.y + yy, tz = dx.z + yz;
-                c = make_float4((tx - dx.x) - yx, (ty - dx.y) - yy, (tz - dx.z) - yz, 0.f);
-                dx = make_float4(tx, ty, tz, 0.f);
-                D.dX[i] = dx;
-                D.dXc[i] = c;
-                // quaternion, q <- normalize(q + dt/2 (0, W) q)
+                float3 v = f3(D.V[i]), w = f3(D.W[i]), dxx = f3(dx), c = f3(D.dXc[i]);
                 float4 q = D.q[i];
-                float dq0 = -(wh.x * q.y + wh.y * q.z + wh.z * q.w);
-                float3 wxv = crossf(f3(wh), make_float3(q.y, q.z, q.w));
-                float4 dq = make_float4(dq0, q.x * wh.x + wxv.x, q.x * wh.y + wxv.y, q.x * wh.z + wxv.z);
-                q = make_float4(q.x + 0.5f * dt * dq.x, q.y + 0.5f * dt * dq.y, q.z + 0.5f * dt * dq.z,
-                                q.w + 0.5f * dt * dq.w);
-                float nq = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-                D.q[i] = make_float4(q.x * nq, q.y * nq, q.z * nq, q.w * nq);
+                float3 vh3, wh3;
+                kick_drift(D, f3(D.Fc[i]), f3(D.Tc[i]), f3(D.Fa[i]), f3(D.Ta[i]), D.invm[i], D.invI[i], v, w, vh3,
+                           wh3, dxx, c, q);
+                vh = make_float4(vh3.x, vh3.y, vh3.z, 0.f);
+                wh = make_float4(wh3.x, wh3.y, wh3.z, 0.f);
+                dx = make_float4(dxx.x, dxx.y, dxx.z, 0.f);
+                D.dX[i] = dx;
+                D.dXc[i] = make_float4(c.x, c.y, c.z, 0.f);
+                D.q[i] = q;
             }
             D.dXb[b * D.n + i] = dx;
             D.Vhb[b * D.n + i] = vh;
@@ -213,7 +287,7 @@ __global__ void k_dem_step(Dem D, int init_only) {
             int i = team + it * nteams;
             bool act = i < D.n && !D.fixed[i];
             float3 F = make_float3(0.f, 0.f, 0.f), T = F;
-            if (act) contact_forces(D, i, b, dt, tl, F, T);
+            if (act) contact_forces(D, i, b, D.dt, tl, F, T);
             team_sum(F, T);
             if (i < D.n && tl == 0) {
                 if (!act) {
@@ -222,14 +296,11 @@ __global__ void k_dem_step(Dem D, int init_only) {
                 }
                 D.Fc[i] = make_float4(F.x, F.y, F.z, 0.f);
                 D.Tc[i] = make_float4(T.x, T.y, T.z, 0.f);
-                float4 vh = D.Vhb[b * D.n + i], wh = D.Whb[b * D.n + i];
-                float im = D.invm[i], iI = D.invI[i];
-                float4 fa = D.Fa[i], ta = D.Ta[i];
-                D.V[i] = make_float4(vh.x + 0.5f * dt * (F.x + fa.x + D.g.x) * im,
-                                     vh.y + 0.5f * dt * (F.y + fa.y + D.g.y) * im,
-                                     vh.z + 0.5f * dt * (F.z + fa.z + D.g.z) * im, 0.f);
-                D.W[i] = make_float4(wh.x + 0.5f * dt * (T.x + ta.x) * iI, wh.y + 0.5f * dt * (T.y + ta.y) * iI,
-                                     wh.z + 0.5f * dt * (T.z + ta.z) * iI, 0.f);
+                float3 v, w;
+                close_kick(D, f3(D.Vhb[b * D.n + i]), f3(D.Whb[b * D.n + i]), F, T, f3(D.Fa[i]), f3(D.Ta[i]),
+                           D.invm[i], D.invI[i], v, w);
+                D.V[i] = make_float4(v.x, v.y, v.z, 0.f);
+                D.W[i] = make_float4(w.x, w.y, w.z, 0.f);
             }
         }
     }
@@ -240,44 +311,221 @@ __global__ void k_dem_step(Dem D, int init_only) {
     for (int it = 0; it < iters; ++it) {
         int i = team + it * nteams;
         if (i >= D.n || tl != 0) continue;
-        float4 dx = D.dX[i], c = D.dXc[i], v = D.V[i];
-        double X0 = D.Xref[3 * i] + (double)dx.x - (double)c.x;
-        double X1 = D.Xref[3 * i + 1] + (double)dx.y - (double)c.y;
-        double X2 = D.Xref[3 * i + 2] + (double)dx.z - (double)c.z;
-        int4 o = make_int4((int)floor(D.Xref[3 * i]), (int)floor(D.Xref[3 * i + 1]),
-                           (int)floor(D.Xref[3 * i + 2]), 0);
-        D.org[i] = o;
-        int wx = D.px ? (int)(((long long)o.x % (long long)D.Lx + (long long)D.Lx) % (long long)D.Lx) : o.x;
-        int wy = (int)(((long long)o.y % (long long)D.Ly + (long long)D.Ly) % (long long)D.Ly);
-        int wz = (int)(((long long)o.z % (long long)D.Lz + (long long)D.Lz) % (long long)D.Lz);
-        D.orgw[i] = make_int4(wx, wy, wz, 0);
-        D.xf[i] = make_float4((float)(X0 - o.x), (float)(X1 - o.y), (float)(X2 - o.z), 0.f);
-        float dd = sqrtf(dx.x * dx.x + dx.y * dx.y + dx.z * dx.z);
-        float vv = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
-        if (!(dd == dd) || !(vv == vv) || isinf(dd) || isinf(vv)) bad |= ST_UNSTABLE;
-        else if (dd >= D.hard_disp) bad |= ST_SKIN;
-        dmax = fmaxf(dmax, dd);
-        vmax = fmaxf(vmax, vv);
+        sphere_frame(D, i, dmax, vmax, bad);
     }
-    const unsigned full = 0xffffffffu;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        dmax = fmaxf(dmax, __shfl_xor_sync(full, dmax, o));
-        vmax = fmaxf(vmax, __shfl_xor_sync(full, vmax, o));
-        bad |= __shfl_xor_sync(full, bad, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (dmax > 0.f) atomicMax(D.max_disp_bits, __float_as_uint(dmax));
-        if (vmax > 0.f) atomicMax(D.max_vel_bits, __float_as_uint(vmax));
-        if (bad) atomicOr(D.status, bad);
-    }
+    flush_maxima(D, dmax, vmax, bad);
     cl.sync();
     if (tid == 0 && !init_only) *D.t_dev += 1ull;
 }
 
+// The same K substeps with every sphere's state in registers of its team and
+// the per-substep exchange (displacement and half-step velocities) in the
+// distributed shared memory of the cluster: one cluster of up to 16 CTAs of
+// DSM_THREADS threads, spc = blockDim / TEAM spheres per CTA, sphere j in CTA
+// j / spc.  The first NBT neighbour entries of each team lane live in
+// registers (with their tangential history) for the whole launch; further
+// entries go through global memory.  Used when every sphere has a team.
+constexpr int DSM_THREADS = 512;
+constexpr int NBT = 3;
+
+__global__ void __launch_bounds__(DSM_THREADS, 1) k_dem_step_dsm(Dem D) {
+    extern __shared__ float4 xchg[];  // [2 substep parities][3: dX, Vh, Wh][spc]
+    cg::cluster_group cl = cg::this_cluster();
+    const int spc = blockDim.x / TEAM;
+    const int tl = threadIdx.x % TEAM, ls = threadIdx.x / TEAM;
+    const int i = blockIdx.x * spc + ls;
+    const bool have = i < D.n;
+    const unsigned full = 0xffffffffu;
+    const int lead = (threadIdx.x & 31) & ~(TEAM - 1);  // lane of the team's first thread
+    const float3 zero = make_float3(0.f, 0.f, 0.f);
+    float3 dx = zero, dxc = zero, v = zero, w = zero, fc = zero, tc = zero;
+    float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
+    float im = 0.f, iI = 0.f, Ri = 1.f;
+    bool fixed = true;
+    int cnt = 0;
+    if (have) {
+        dx = f3(D.dX[i]);
+        dxc = f3(D.dXc[i]);
+        v = f3(D.V[i]);
+        w = f3(D.W[i]);
+        q = D.q[i];
+        fc = f3(D.Fc[i]);
+        tc = f3(D.Tc[i]);
+        im = D.invm[i];
+        iI = D.invI[i];
+        Ri = D.R[i];
+        fixed = D.fixed[i] != 0;
+        cnt = D.nb_cnt[i];
+    }
+    // hydrodynamic drive: the mean of this and the previous step's exchange
+    // sums (the team's first thread sums the replicas, the team shares it)
+    float3 fa = zero, ta = zero;
+    if (have && tl == 0) {
+        double f[3] = {0.0, 0.0, 0.0}, t[3] = {0.0, 0.0, 0.0};
+        for (int r = 0; r < NREP; ++r)
+            for (int a = 0; a < 3; ++a) {
+                f[a] += D.Fh[3 * ((size_t)r * D.n + i) + a];
+                t[a] += D.Th[3 * ((size_t)r * D.n + i) + a];
+            }
+        fa = make_float3((float)(0.5 * (f[0] + D.Fh_prev[3 * i])), (float)(0.5 * (f[1] + D.Fh_prev[3 * i + 1])),
+                         (float)(0.5 * (f[2] + D.Fh_prev[3 * i + 2])));
+        ta = make_float3((float)(0.5 * (t[0] + D.Th_prev[3 * i])), (float)(0.5 * (t[1] + D.Th_prev[3 * i + 1])),
+                         (float)(0.5 * (t[2] + D.Th_prev[3 * i + 2])));
+        for (int a = 0; a < 3; ++a) {
+            D.Fh_prev[3 * i + a] = f[a];
+            D.Th_prev[3 * i + a] = t[a];
+        }
+        D.Fa[i] = make_float4(fa.x, fa.y, fa.z, 0.f);
+        D.Ta[i] = make_float4(ta.x, ta.y, ta.z, 0.f);
+    }
+    fa = make_float3(__shfl_sync(full, fa.x, lead), __shfl_sync(full, fa.y, lead), __shfl_sync(full, fa.z, lead));
+    ta = make_float3(__shfl_sync(full, ta.x, lead), __shfl_sync(full, ta.y, lead), __shfl_sync(full, ta.z, lead));
+    // this lane's neighbour entries tl + u TEAM, u < NBT
+    int nj[NBT];
+    float4 ndr[NBT];
+    float3 nh[NBT];
+#pragma unroll
+    for (int u = 0; u < NBT; ++u) {
+        int k = tl + u * TEAM;
+        nj[u] = -1;
+        if (k < cnt) {
+            size_t e = (size_t)i * D.nbmax + k;
+            nj[u] = D.nb_j[e];
+            ndr[u] = D.nb_dref[e];
+            nh[u] = f3(D.nb_ft[e]);
+        }
+    }
+    for (int s = 0; s < D.K; ++s) {
+        const int b = s & 1;
+        float3 vh = zero, wh = zero;
+        if (!fixed) kick_drift(D, fc, tc, fa, ta, im, iI, v, w, vh, wh, dx, dxc, q);
+        if (have && tl == 0) {
+            xchg[(b * 3 + 0) * spc + ls] = make_float4(dx.x, dx.y, dx.z, 0.f);
+            xchg[(b * 3 + 1) * spc + ls] = make_float4(vh.x, vh.y, vh.z, 0.f);
+            xchg[(b * 3 + 2) * spc + ls] = make_float4(wh.x, wh.y, wh.z, 0.f);
+        }
+        cl.sync();
+        float3 F = zero, T = zero;
+        if (have && !fixed) {
+#pragma unroll
+            for (int u = 0; u < NBT; ++u) {
+                if (nj[u] < 0) continue;
+                int rk = nj[u] / spc, lj = nj[u] - rk * spc;
+                const float4* rx = cl.map_shared_rank(xchg, rk);
+                float4 xj = rx[(b * 3 + 0) * spc + lj], vj = rx[(b * 3 + 1) * spc + lj],
+                       wj = rx[(b * 3 + 2) * spc + lj];
+                float4 h = make_float4(nh[u].x, nh[u].y, nh[u].z, 0.f);
+                pair_contact(D, Ri, __ldg(&D.R[nj[u]]), make_float3(xj.x - dx.x, xj.y - dx.y, xj.z - dx.z), ndr[u],
+                             vh, wh, f3(vj), f3(wj), D.dt, h, F, T);
+                nh[u] = f3(h);
+            }
+            for (int k = tl + NBT * TEAM; k < cnt; k += TEAM) {  // entries beyond the registers
+                size_t e = (size_t)i * D.nbmax + k;
+                int j = D.nb_j[e];
+                int rk = j / spc, lj = j - rk * spc;
+                const float4* rx = cl.map_shared_rank(xchg, rk);
+                float4 h = D.nb_ft[e];
+                float4 xjj = rx[(b * 3 + 0) * spc + lj];
+                pair_contact(D, Ri, D.R[j], make_float3(xjj.x - dx.x, xjj.y - dx.y, xjj.z - dx.z), D.nb_dref[e], vh,
+                             wh, f3(rx[(b * 3 + 1) * spc + lj]), f3(rx[(b * 3 + 2) * spc + lj]), D.dt, h, F, T);
+                D.nb_ft[e] = h;
+            }
+        }
+        team_sum(F, T);
+        if (fixed) {
+            v = w = zero;
+        } else {
+            fc = F;
+            tc = T;
+            close_kick(D, vh, wh, F, T, fa, ta, im, iI, v, w);
+        }
+    }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
+    if (have) {
+#pragma unroll
+        for (int u = 0; u < NBT; ++u)
+            if (nj[u] >= 0) D.nb_ft[(size_t)i * D.nbmax + tl + u * TEAM] = make_float4(nh[u].x, nh[u].y, nh[u].z, 0.f);
+        if (tl == 0) {
+            D.dX[i] = make_float4(dx.x, dx.y, dx.z, 0.f);
+            D.dXc[i] = make_float4(dxc.x, dxc.y, dxc.z, 0.f);
+            D.V[i] = make_float4(v.x, v.y, v.z, 0.f);
+            D.W[i] = make_float4(w.x, w.y, w.z, 0.f);
+            D.q[i] = q;
+            D.Fc[i] = make_float4(fc.x, fc.y, fc.z, 0.f);
+            D.Tc[i] = make_float4(tc.x, tc.y, tc.z, 0.f);
+        }
+    }
+    float dmax = 0.f, vmax = 0.f;
+    uint32_t bad = 0;
+    if (have && tl == 0) sphere_frame(D, i, dmax, vmax, bad);
+    flush_maxima(D, dmax, vmax, bad);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *D.t_dev += 1ull;
+}
+
+// Largest cluster (CTAs of DSM_THREADS threads) the DSM kernel can run with
+// on each device, found on the first initialisation launch (outside any
+// stream capture); 0 = not found (the general kernel serves).
+static int g_dsm_cluster[64];
+static bool g_dsm_probed[64];
+
+static void probe_dsm(int dev) {
+    if (dev < 0 || dev >= 64 || g_dsm_probed[dev]) return;
+    g_dsm_probed[dev] = true;
+    g_dsm_cluster[dev] = 0;
+    if (cudaFuncSetAttribute(k_dem_step_dsm, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    for (int C : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(C, 1, 1);
+        cfg.blockDim = dim3(DSM_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = 6 * (DSM_THREADS / TEAM) * sizeof(float4);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, k_dem_step_dsm, &cfg) == cudaSuccess && ncl > 0) {
+            g_dsm_cluster[dev] = C;
+            break;
+        }
+        cudaGetLastError();
+    }
+}
+
 void launch_dem_step(const Dem& D, bool init_only, cudaStream_t s) {
-    // TEAM threads per sphere, up to 8 CTAs of up to 1024 threads
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (init_only) probe_dsm(dev);
     long long need = (long long)TEAM * (D.n > 0 ? D.n : 1);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int cmax = dev >= 0 && dev < 64 ? g_dsm_cluster[dev] : 0;
+    if (!init_only && cmax > 0 && need <= (long long)cmax * DSM_THREADS) {
+        int C = 1, T = (int)(((need + 31) / 32) * 32);
+        if (need > DSM_THREADS) {
+            C = (int)((need + DSM_THREADS - 1) / DSM_THREADS);
+            T = DSM_THREADS;
+        }
+        cfg.gridDim = dim3(C, 1, 1);
+        cfg.blockDim = dim3(T, 1, 1);
+        cfg.dynamicSmemBytes = 6 * (T / TEAM) * sizeof(float4);
+        attr[0].val.clusterDim.x = C;
+        cudaLaunchKernelEx(&cfg, k_dem_step_dsm, D);
+        return;
+    }
+    // general kernel: TEAM threads per sphere, up to 8 CTAs of up to 1024
+    // threads, several spheres per team when needed
     int C = 1;
     int T = (int)(((need + 31) / 32) * 32);
     if (T > 256) {
@@ -286,18 +534,10 @@ void launch_dem_step(const Dem& D, bool init_only, cudaStream_t s) {
         T = ((T + 31) / 32) * 32;
         if (T > 1024) T = 1024;
     }
-    cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
     cfg.blockDim = dim3(T, 1, 1);
     cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, k_dem_step, D, init_only ? 1 : 0);
 }
 

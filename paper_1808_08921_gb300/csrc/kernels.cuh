@@ -28,23 +28,29 @@ struct BC {
     const unsigned long long* t_dev;
 };
 
-// Link lists for the link kernel, grouped by (sphere, direction) and padded
-// to LINK_WARP records, so a warp walks LINK_WARP links of one sphere in one
-// direction (LINK_WARP / 32 per thread):
-//   warp_pd[w] = sphere << 5 | direction m  (the solid neighbour is x + c_m)
-//   link[k]    = {cidx of the fluid node x,
-//                 (x - org) + 128 packed 8 bits per axis | maybe << 24 |
-//                 shared << 25}
+// Link lists for the link kernel.  Links are grouped by (sphere, direction
+// m), each group padded to whole chunks of 32 records, and each sphere's
+// groups together padded to whole LINK_WARP records, so a warp walks
+// LINK_WARP / 32 chunks of one sphere, each chunk in one direction (one
+// record per lane and chunk):
+//   warp_p[w]    = sphere index
+//   warp_dirs[w] = direction m of chunk k in byte k (the solid neighbour is
+//                  x + c_m), | 128 when the chunk holds a flagged link
+//   link[r]      = {cidx of the fluid node x,
+//                   (x - org) + 128 packed 8 bits per axis | maybe << 24 |
+//                   shared << 25 | in_band << 26}
 // `maybe` marks a neighbour inside a band: whether the sphere owns it now
 // is decided by the map update's FP32 test (same operands and rounding),
 // or by reading the owner map near the FP32 margin or when the band node
-// has several candidate spheres (`shared`).  The other links are fixed until
-// the next re-layout.  cidx == NONE pads.
+// has several candidate spheres (`shared`).  `in_band` marks a fluid node x
+// that may itself be covered before the next re-layout (its fluid bit is
+// read); every other link node stays fluid.  cidx == NONE pads.
 constexpr int LINK_WARP = 128;
 
 struct LinkLists {
     const uint2* link;
-    const uint32_t* warp_pd;
+    const uint32_t* warp_p;
+    const uint32_t* warp_dirs;
     uint32_t nwarps;
 };
 

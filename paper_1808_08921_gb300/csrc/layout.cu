@@ -231,11 +231,14 @@ __global__ void k_band_collect(LayoutArgs A, uint32_t* band_coord, uint32_t* cou
 // link lists: for every stored node x within R + skin + 1.5 of a sphere and
 // every direction m, a link if x + c_m is owned by the sphere and outside
 // every band (fixed until the next re-layout), or a `maybe` link if x + c_m
-// is a band node within R + skin of the sphere (owner read each step).
+// is a band node within R + skin of the sphere (owner read each step).  A
+// link node x that is itself in a band carries `in_band` (its fluid bit is
+// read each step).
 struct SurfNode {
     uint32_t ci;
     int ox, oy, oz;           // x - floor(Xref)
     uint32_t sure, maybe, shared;
+    bool in_band;
 };
 
 __device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, long long t, int x0, int y0, int z0,
@@ -259,6 +262,7 @@ __device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, long long t,
     bool fl;
     uint32_t ci = stored_index(A.L, x, y, z, fl);
     if (ci == NONE) return false;
+    const bool in_band = A.band[((size_t)x * A.L.ny + y) * A.L.nz + z] != 0;
     double Rb = Rp + A.skin;
     uint32_t sure = 0, maybe = 0, shared = 0;
 #pragma unroll
@@ -286,10 +290,12 @@ __device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, long long t,
     sn.sure = sure;
     sn.maybe = maybe;
     sn.shared = shared;
+    sn.in_band = in_band;
     return true;
 }
 
-// per sphere: links per direction (padded to whole warps)
+// per sphere: links per direction, padded to whole 32-record chunks; the
+// sphere's total is padded to whole LINK_WARP groups on its last direction
 __global__ void k_surf_count(SurfArgs A) {
     int p = blockIdx.x;
     double reach = A.R[p] + A.reach_extra;
@@ -309,8 +315,18 @@ __global__ void k_surf_count(SurfArgs A) {
             if (bits >> m & 1u) atomicAdd(&cnt[m], 1u);
     }
     __syncthreads();
-    if (threadIdx.x < Q - 1)
-        A.count[(size_t)p * (Q - 1) + threadIdx.x] = (cnt[threadIdx.x] + (LINK_WARP - 1)) / LINK_WARP * LINK_WARP;
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0, raw = 0;
+        for (int m = 0; m < Q - 1; ++m) {
+            raw += cnt[m];
+            cnt[m] = (cnt[m] + 31u) / 32u * 32u;
+            tot += cnt[m];
+        }
+        atomicAdd(A.nlink, raw);
+        cnt[Q - 2] += (tot + (LINK_WARP - 1)) / LINK_WARP * LINK_WARP - tot;
+    }
+    __syncthreads();
+    if (threadIdx.x < Q - 1) A.count[(size_t)p * (Q - 1) + threadIdx.x] = cnt[threadIdx.x];
 }
 
 // fill in a deterministic order: per direction, chunks of blockDim nodes in
@@ -357,21 +373,34 @@ __global__ void k_surf_fill(SurfArgs A) {
                 if (!(bits >> m & 1u)) continue;
                 size_t g = (size_t)p * (Q - 1) + m;
                 uint32_t pos = A.offset[g] + run[m] + sh[m][wid] + before[m];
-                A.link[pos] = make_uint2(sn.ci, rel | ((sn.maybe >> m & 1u) << 24) | ((sn.shared >> m & 1u) << 25));
+                A.link[pos] = make_uint2(sn.ci, rel | ((sn.maybe >> m & 1u) << 24) | ((sn.shared >> m & 1u) << 25) |
+                                                    ((uint32_t)sn.in_band << 26));
             }
         }
         __syncthreads();
         if (threadIdx.x < Q - 1) run[threadIdx.x] += sh[threadIdx.x][32];
         __syncthreads();
     }
-    // pad each (sphere, direction) group and tag its warps
+    // pad every (sphere, direction) group to its chunks
     for (int m = 0; m < Q - 1; ++m) {
         size_t g = (size_t)p * (Q - 1) + m;
         uint32_t base = A.offset[g], end = base + A.count[g];
         for (uint32_t k = base + run[m] + threadIdx.x; k < end; k += blockDim.x) A.link[k] = make_uint2(NONE, 0u);
-        for (uint32_t k = base / LINK_WARP + threadIdx.x; k < end / LINK_WARP; k += blockDim.x)
-            A.warp_pd[k] = ((uint32_t)p << 5) | (uint32_t)m;
     }
+    __syncthreads();
+    // label the chunks with their direction (| 128 when a chunk holds a
+    // flagged link: maybe, shared or in_band) and tag the sphere's warps
+    for (int m = 0; m < Q - 1; ++m) {
+        size_t g = (size_t)p * (Q - 1) + m;
+        uint32_t base = A.offset[g], end = base + A.count[g];
+        for (uint32_t k = base / 32 + wid; k < end / 32; k += nwarp) {
+            uint32_t fl = __ballot_sync(0xffffffffu, ((A.link[32 * k + lane].y >> 24) & 7u) != 0u);
+            if (lane == 0) A.chunk_dir[k] = (uint8_t)(m | (fl ? 128 : 0));
+        }
+    }
+    uint32_t first = A.offset[(size_t)p * (Q - 1)];
+    uint32_t last = A.offset[(size_t)p * (Q - 1) + Q - 2] + A.count[(size_t)p * (Q - 1) + Q - 2];
+    for (uint32_t k = first / LINK_WARP + threadIdx.x; k < last / LINK_WARP; k += blockDim.x) A.warp_p[k] = (uint32_t)p;
 }
 
 __global__ void k_fill_u64(unsigned long long* p, unsigned long long v, size_t n) {

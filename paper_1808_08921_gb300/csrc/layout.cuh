@@ -36,10 +36,13 @@ struct SurfArgs {
     double skin;
     const int32_t* owner;   // map at layout time
     const uint8_t* band;    // band flags at layout time
-    uint32_t* count;        // [n * 18] links per (sphere, direction), padded to 32
+    uint32_t* count;        // [n * 18] links per (sphere, direction), padded to 32; the
+                            // last direction of a sphere also holds the padding to LINK_WARP
     const uint32_t* offset; // exclusive scan of count
     uint2* link;
-    uint32_t* warp_pd;
+    uint32_t* warp_p;
+    uint8_t* chunk_dir;     // direction of every 32-record chunk (4 per warp)
+    uint32_t* nlink;        // total link records before padding (accumulated)
 };
 
 struct CellGrid {

@@ -216,7 +216,7 @@ class Sim:
     def counters(self):
         out = np.zeros(10, np.int64)
         self._check(load().lbm_dem_read_counters(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
-        keys = ("nodes", "stored", "fluid", "band", "surface_entries", "neighbour_entries", "t",
+        keys = ("nodes", "stored", "fluid", "band", "links", "neighbour_entries", "t",
                 "relayouts", "conversions", "launches")
         return dict(zip(keys, (int(v) for v in out)))
 
