@@ -154,7 +154,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
     w = workloads.config_scale(steps=args.steps)
     stream = torch.cuda.current_stream()
-    over = dict(device=dev, cuda_stream=stream.cuda_stream, skin=0.1, dem_skin=0.5)
+    storage = {"f32": lbmdem.F32, "bf16": lbmdem.BF16_DEV, "f16": lbmdem.F16_DEV}[args.storage]
+    over = dict(device=dev, cuda_stream=stream.cuda_stream, skin=0.1, dem_skin=0.5, storage=storage)
     sim = lbmdem.Sim.from_workload(w, **over)
     cnt0 = sim.counters()
     sim.step(args.warmup)
@@ -197,8 +198,10 @@ def run_ours(args):
     # population read and the bounced value written); the dominant one by
     # measured time is the headline `roofline`
     peak, peak_kind = _peaks()
-    algo = {"collide_stream": (BYTES_PER_FLUID_NODE, fluid, "fluid node"),
-            "links": (BYTES_PER_LINK, cnt_b["links"], "link record")}
+    esz = 4 if args.storage == "f32" else 2  # bytes per stored population
+    node_bytes = BYTES_PER_FLUID_NODE * esz // 4
+    algo = {"collide_stream": (node_bytes, fluid, "fluid node"),
+            "links": (BYTES_PER_LINK * esz // 4, cnt_b["links"], "link record")}
     kernels = {}
     for g, (per, units, uname) in algo.items():
         k_ms, k_n = tm[g]
@@ -210,11 +213,11 @@ def run_ours(args):
                       "work_unit": uname, "us_per_launch": round(1e3 * avg, 2), "peak_kind": peak_kind}
     dom = max(kernels, key=lambda g: kernels[g]["us_per_launch"])
     roofline = dict(kernels[dom], kernel=dom)
-    step_bytes = BYTES_PER_FLUID_NODE * fluid_sum
+    step_bytes = node_bytes * fluid_sum
     step_ach = step_bytes * args.steps / (ms_max * 1e-3) / 1e9
     step_roofline = {"bytes_per_step": step_bytes, "achieved": round(step_ach, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(step_ach / peak, 4),
-                     "note": "whole coupled step at 152 B per fluid node (all kernels in the time)"}
+                     "note": "whole coupled step at the collide+stream bytes per fluid node (all kernels in the time)"}
     # end to end through the C ABI from host buffers
     e2e = None
     if not args.no_e2e:
@@ -254,6 +257,9 @@ def run_ours(args):
                        "mlups_all_nodes": round(value * cnt_b["nodes"] / max(fluid, 1), 1),
                        "l2": "inputs larger than L2: populations %.0f MB" % (19 * 4 * cnt_b["stored"] / 1e6),
                        "relayouts_in_timed_region": cnt_b["relayouts"] - cnt_a["relayouts"],
+                       "conversions_in_timed_region": cnt_b["conversions"] - cnt_a["conversions"],
+                       "link_records": cnt_b["links"],
+                       "population_storage": args.storage,
                        "status": st},
             "roofline": roofline,
             "step_roofline": step_roofline,
@@ -362,6 +368,8 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
+                    help="population storage (deviations; the arithmetic is FP32 in every case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

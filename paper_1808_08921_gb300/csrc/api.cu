@@ -84,7 +84,7 @@ struct lbmdem_ctx {
     DBuf<uint8_t> deep, band;
     DBuf<uint4> rec, rec2;
     DBuf<uint32_t> maskB, maskB2, cntA, cntB, scan_tmp;
-    DBuf<float> f, f2;
+    DBuf<uint8_t> f, f2;  // populations, 4 or 2 bytes each
     DBuf<uint32_t> coord, fbits;
     uint32_t nA = 0, nS = 0, nSpad = 0;
     DBuf<uint32_t> band_coord, band_count;
@@ -93,7 +93,7 @@ struct lbmdem_ctx {
     DBuf<uint32_t> surf_count, surf_off;
     DBuf<uint2> surf_link;
     DBuf<uint32_t> warp_p;
-    DBuf<uint32_t> warp_dirs;  // 4 chunk directions per warp
+    DBuf<uint8_t> chunk_dir;  // direction (| flag) of every 32-record chunk
     uint32_t nwarps = 0;
     uint32_t nlink_raw = 0;  // link records before padding
     DBuf<Flip> flip_rec;
@@ -192,6 +192,9 @@ static Lat make_lat(lbmdem_ctx* c) {
     L.nS = c->nS;
     L.nSpad = c->nSpad;
     L.f = c->f.p;
+    L.st = c->p.storage == LBMDEM_BF16_DEV ? 1 : c->p.storage == LBMDEM_F16_DEV ? 2 : 0;
+    L.fs = L.st == 2 ? 4096.0f : 1.0f;  // FP16: deviations 1e-8 .. 16 stay normal
+    L.fsi = 1.0f / L.fs;
     L.rec = c->rec.p;
     L.maskB = c->maskB.p;
     L.coord = c->coord.p;
@@ -400,8 +403,9 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
     launch_coords(LA, nA, nSpad, c->fbits.p, s);
     CK(cudaGetLastError());
     // populations
-    CK(c->f2.alloc((size_t)Q * nSpad));
-    CK(cudaMemsetAsync(c->f2.p, 0, sizeof(float) * Q * nSpad, s));
+    const size_t esz = c->p.storage == LBMDEM_F32 ? 4 : 2;
+    CK(c->f2.alloc((size_t)Q * nSpad * esz));
+    CK(cudaMemsetAsync(c->f2.p, 0, esz * Q * nSpad, s));  // zero deviations: rest at rho_f
     Lat Lnew = make_lat(c);
     Lnew.nA = nA;
     Lnew.nS = nS;
@@ -462,11 +466,11 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
     if (int r = read_u32(c, c->surf_count.p + ng + 1, &c->nlink_raw)) return r;
     CK(c->surf_link.ensure(std::max<uint32_t>(nlink, 32)));
     CK(c->warp_p.ensure(std::max<uint32_t>(nlink / LINK_WARP, 1)));
-    CK(c->warp_dirs.ensure(std::max<uint32_t>(nlink / LINK_WARP, 1)));
+    CK(c->chunk_dir.ensure(std::max<uint32_t>(nlink / 32, LINK_CHUNKS)));
     SA.offset = c->surf_off.p;
     SA.link = c->surf_link.p;
     SA.warp_p = c->warp_p.p;
-    SA.chunk_dir = reinterpret_cast<uint8_t*>(c->warp_dirs.p);
+    SA.chunk_dir = c->chunk_dir.p;
     launch_surf_fill(SA, np, s);
     CK(cudaGetLastError());
     c->nwarps = nlink / LINK_WARP;
@@ -568,7 +572,7 @@ static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
         if (tm) record_pair_begin(c, 0, e);
         launch_collide(L, mon, parity == 1, monitor, s);
         if (tm) record_pair_end(c, e);
-        LinkLists LL{c->surf_link.p, c->warp_p.p, c->warp_dirs.p, c->nwarps};
+        LinkLists LL{c->surf_link.p, c->warp_p.p, c->chunk_dir.p, c->nwarps};
         if (tm) record_pair_begin(c, 1, e);
         launch_links(L, P, LL, s);
         if (tm) record_pair_end(c, e);
@@ -726,7 +730,8 @@ int lbm_dem_init(const lbmdem_params* pp, lbmdem_ctx** out) {
     if (p.nx < 1 || p.ny < 1 || p.nz < 1 || p.nx > 4096 || p.ny > 1024 || p.nz > 1024)
         return LBMDEM_ERR_INVALID_ARG;
     if (!(p.tau > 0.5) || !(p.rho_f > 0) || p.dem_substeps < 1) return LBMDEM_ERR_INVALID_ARG;
-    if (p.storage != LBMDEM_F32) return LBMDEM_ERR_INVALID_ARG;
+    if (p.storage != LBMDEM_F32 && p.storage != LBMDEM_BF16_DEV && p.storage != LBMDEM_F16_DEV)
+        return LBMDEM_ERR_INVALID_ARG;
     if (p.inlet < 0 || p.inlet > 2 || p.outlet < 0 || p.outlet > 2) return LBMDEM_ERR_INVALID_ARG;
     if (p.inlet != LBMDEM_X_PERIODIC && p.nx < 3) return LBMDEM_ERR_INVALID_ARG;
     if (p.probe_x >= p.nx || p.probe_x < -1) return LBMDEM_ERR_INVALID_ARG;

@@ -9,8 +9,11 @@
 //          time (lexicographic x, y, z order, indices [0, nA)) and B = the
 //          remaining stored nodes (indices [nA, nS)), so the streamed region A
 //          is dense in fluid and B is only touched where a node converted.
-//   * f  = populations as deviations g_i = f_i - w_i rho_f (FP32), structure
-//          of arrays [19][nSpad], in place with the AA access pattern.
+//   * f  = populations as deviations g_i = f_i - w_i rho_f, structure of
+//          arrays [19][nSpad], in place with the AA access pattern; stored as
+//          FP32, or as BF16 / FP16 scaled by a power of two (FP16: 2^12, so
+//          that deviations of 1e-8 .. 16 stay normal numbers), always
+//          collided in FP32.
 //   * rec[w] = {maskF, maskA, baseA, baseB} for every 32-node word of a
 //          z-line: fluid-now bits, region-A bits and the compact indices of the
 //          first A and B node of the word; maskB[w] holds the B bits.  The
@@ -34,6 +37,8 @@
 //   the inlet/outlet overwrite them.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -98,7 +103,9 @@ struct Lat {
     int nx, ny, nz, nw;   // nw = 32-node words per z-line
     int px;               // x periodic
     uint32_t nA, nS, nSpad;
-    float* f;             // [19][nSpad] deviations
+    void* f;              // [19][nSpad] deviations, element type by `st`
+    int st;               // storage: 0 FP32, 1 BF16, 2 FP16 (scaled by fs)
+    float fs, fsi;        // storage scale and its inverse (powers of two)
     uint4* rec;           // [nx*ny*nw] {maskF, maskA, baseA, baseB}
     uint32_t* maskB;      // [nx*ny*nw]
     uint32_t* coord;      // [nSpad]
@@ -148,15 +155,38 @@ __device__ __forceinline__ bool fluid_bit(const Lat& L, uint32_t i) {
     return (L.fbits[i >> 5] >> (i & 31)) & 1u;
 }
 
+// Population storage types and their FP32 conversions (round to nearest;
+// the scale is a power of two, so scaling is exact).
+template <int ST> struct PopT;
+template <> struct PopT<0> { using T = float; };
+template <> struct PopT<1> { using T = __nv_bfloat16; };
+template <> struct PopT<2> { using T = __half; };
+
+template <int ST> __device__ __forceinline__ float to_f(typename PopT<ST>::T v, float fsi);
+template <> __device__ __forceinline__ float to_f<0>(float v, float) { return v; }
+template <> __device__ __forceinline__ float to_f<1>(__nv_bfloat16 v, float fsi) { return __bfloat162float(v) * fsi; }
+template <> __device__ __forceinline__ float to_f<2>(__half v, float fsi) { return __half2float(v) * fsi; }
+
+template <int ST> __device__ __forceinline__ typename PopT<ST>::T from_f(float v, float fs);
+template <> __device__ __forceinline__ float from_f<0>(float v, float) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<1>(float v, float fs) { return __float2bfloat16_rn(v * fs); }
+template <> __device__ __forceinline__ __half from_f<2>(float v, float fs) { return __float2half_rn(v * fs); }
+
+template <int ST> __device__ __forceinline__ typename PopT<ST>::T* pops(const Lat& L) {
+    return static_cast<typename PopT<ST>::T*>(L.f);
+}
+
 // Location of population m of fluid node (x,y,z) with compact index i, in the
-// state between steps.  parity_odd = true: the state after an even step
+// state between steps.  after_even = true: the state after an even step
 // (natural populations sit in the neighbours' reversed slots).
-__device__ __forceinline__ float* pop_loc(const Lat& L, bool after_even, int x, int y, int z,
-                                          uint32_t i, int m) {
-    if (!after_even || m == 18) return L.f + (size_t)m * L.nSpad + i;
+template <int ST>
+__device__ __forceinline__ typename PopT<ST>::T* pop_loc(const Lat& L, bool after_even, int x, int y, int z,
+                                                         uint32_t i, int m) {
+    typename PopT<ST>::T* f = pops<ST>(L);
+    if (!after_even || m == 18) return f + (size_t)m * L.nSpad + i;
     uint32_t s = fluid_index(L, x, y, z, -cx(m), -cy(m), -cz(m));
-    if (s == NONE) return L.f + (size_t)m * L.nSpad + i;
-    return L.f + (size_t)opp(m) * L.nSpad + s;
+    if (s == NONE) return f + (size_t)m * L.nSpad + i;
+    return f + (size_t)opp(m) * L.nSpad + s;
 }
 
 // Particles as seen by the lattice kernels (current time level).

@@ -89,7 +89,11 @@ __constant__ DirC kDir[Q - 1] = {
 #undef LBMDEM_DIR
 };
 
-static_assert(LINK_WARP == 4 * 32, "the warp table holds four chunk directions");
+// the LINK_CHUNKS direction bytes of warp w, in one load
+__device__ __forceinline__ unsigned long long warp_chunk_dirs(const LinkLists& B, uint32_t w) {
+    if (LINK_CHUNKS == 8) return *reinterpret_cast<const unsigned long long*>(B.chunk_dir + (size_t)w * 8);
+    return *reinterpret_cast<const uint32_t*>(B.chunk_dir + (size_t)w * 4);
+}
 
 // b - 128 for the byte b at bit `shift` of a record word, exactly, as FP32
 // (2^23 + b from the bits, minus 2^23 + 128: no conversion instruction).
@@ -127,13 +131,15 @@ __device__ __forceinline__ bool owns_neighbour(const Lat& L, const PartView& P, 
 // beta = 6 w rho_f (c x W) (b = r + c/2 and c.(W x c) = 0).  Warp-shuffle
 // sums, then one FP64 atomic per component per warp into one of NREP
 // accumulator copies of the sphere.
+template <int ST>
 __global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
-    constexpr int K = LINK_WARP / 32;
+    constexpr int K = LINK_CHUNKS;
+    auto* f = pops<ST>(L);
     const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= B.nwarps) return;  // whole warps
     const uint32_t lane = threadIdx.x & 31;
     const int p = (int)B.warp_p[w];
-    const uint32_t dirs = B.warp_dirs[w];
+    const unsigned long long dirs = warp_chunk_dirs(B, w);
     const uint2* rec = B.link + (size_t)w * LINK_WARP + lane;
     uint2 lk[K];
 #pragma unroll
@@ -143,7 +149,7 @@ __global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
     bool on[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) on[k] = lk[k].x != NONE;
-    if (dirs & 0x80808080u) {  // some chunk holds flagged links
+    if (dirs & 0x8080808080808080ull) {  // some chunk holds flagged links
         uint32_t fb[K];
 #pragma unroll
         for (int k = 0; k < K; ++k)  // only a node inside a band can have been covered
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int op = kDir[(dirs >> (8 * k)) & 31u].op;
-        v[k] = on[k] ? L.f[(size_t)op * L.nSpad + lk[k].x] : 0.f;
+        v[k] = on[k] ? to_f<ST>(f[(size_t)op * L.nSpad + lk[k].x], L.fsi) : 0.f;
     }
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const float s6 = 6.0f * L.rho_f;
@@ -175,7 +181,7 @@ __global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
         const uint32_t y = lk[k].y;
         const float rx = rel_f(y, 0) - xf.x, ry = rel_f(y, 8) - xf.y, rz = rel_f(y, 16) - xf.z;
         const float delta = alpha + (rx * bx + ry * by + rz * bz);
-        L.f[(size_t)d.op * L.nSpad + lk[k].x] = v[k] - delta;
+        f[(size_t)d.op * L.nSpad + lk[k].x] = from_f<ST>(v[k] - delta, L.fs);
         const float q = 2.0f * v[k] - delta;
         const float qx = d.cx * q, qy = d.cy * q, qz = d.cz * q;
         acc[0] += qx;
@@ -207,7 +213,10 @@ __global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
 void launch_links(const Lat& L, const PartView& P, const LinkLists& B, cudaStream_t s) {
     if (B.nwarps == 0) return;
     uint64_t threads = (uint64_t)B.nwarps * 32;  // one warp per LINK_WARP links
-    k_links<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(L, P, B);
+    unsigned blocks = (unsigned)((threads + 255) / 256);
+    if (L.st == 0) k_links<0><<<blocks, 256, 0, s>>>(L, P, B);
+    else if (L.st == 1) k_links<1><<<blocks, 256, 0, s>>>(L, P, B);
+    else k_links<2><<<blocks, 256, 0, s>>>(L, P, B);
 }
 
 // ------------------------------------------------------------ map update
@@ -330,9 +339,11 @@ __global__ void k_map_band(MapArgs A) {
 // j < 18 is the neighbour x + c_j and j = 18 the node itself; the block's
 // first thread then applies the conversion.
 constexpr int MAP_THREADS = 384;  // >= 19 * 19
+template <int ST>
 __global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
     const Lat& L = A.L;
     __shared__ float sg[Q * Q];
+    __shared__ float srho[Q];
     __shared__ int sv[Q];
     const uint32_t nf = min(A.st->nflip[A.par], A.F.cap);
     const int t = threadIdx.x, j = t / Q, m = t % Q;
@@ -352,7 +363,7 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
                 bool fl;
                 uint32_t ci = stored_index(L, xs, ys, zs, fl);
                 if (fl && ci != NONE) {
-                    g = *pop_loc(L, A.after_even, xs, ys, zs, ci, m);
+                    g = to_f<ST>(*pop_loc<ST>(L, A.after_even, xs, ys, zs, ci, m), L.fsi);
                     valid = true;
                 }
             }
@@ -361,14 +372,18 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
             if (m == 0) sv[j] = valid ? 1 : 0;
         }
         __syncthreads();
+        if (t < Q) {  // density of each gathered node
+            float d = 0.f;
+            for (int mm = 0; mm < Q; ++mm) d += sg[t * Q + mm];
+            srho[t] = L.rho_f + d;
+        }
+        __syncthreads();
         if (t == 0) {
             // mean density of the fluid neighbours (not the node itself)
             float rs = 0.f, rc = 0.f;
             for (int jj = 0; jj < Q - 1; ++jj) {
                 if (!sv[jj]) continue;
-                float d = 0.f;
-                for (int mm = 0; mm < Q; ++mm) d += sg[jj * Q + mm];
-                rs += L.rho_f + d;
+                rs += srho[jj];
                 rc += 1.f;
             }
             int o = f.old_owner, nw = f.new_owner;
@@ -460,6 +475,7 @@ __device__ void map_commit_one(const MapArgs& A, uint32_t k) {
 
 // One block per queued node: thread t < 361 writes population m = t % 19 of
 // node j = t / 19 back with the new map.
+template <int ST>
 __global__ void __launch_bounds__(MAP_THREADS) k_map_scatter(MapArgs A) {
     const Lat L = A.L;
     const uint32_t nf = min(A.st->nflip[A.par], A.F.cap);
@@ -475,7 +491,7 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map_scatter(MapArgs A) {
         bool fl;
         uint32_t ci = stored_index(L, xs, ys, zs, fl);
         if (!fl || ci == NONE) continue;
-        *pop_loc(L, A.after_even, xs, ys, zs, ci, m) = A.F.scratch[(size_t)w * Q * Q + t];
+        *pop_loc<ST>(L, A.after_even, xs, ys, zs, ci, m) = from_f<ST>(A.F.scratch[(size_t)w * Q * Q + t], L.fs);
     }
 }
 
@@ -488,9 +504,13 @@ void launch_map_update(const Lat& L, const PartView& P, const Band& band, const 
     if (band.n == 0) return;
     // the queued count is read on the device: fixed grids stride over it
     const unsigned grid = 2 * 152;
-    k_map_gather_convert<<<grid, MAP_THREADS, 0, s>>>(A);
+    if (L.st == 0) k_map_gather_convert<0><<<grid, MAP_THREADS, 0, s>>>(A);
+    else if (L.st == 1) k_map_gather_convert<1><<<grid, MAP_THREADS, 0, s>>>(A);
+    else k_map_gather_convert<2><<<grid, MAP_THREADS, 0, s>>>(A);
     k_map_commit<<<grid, 256, 0, s>>>(A);
-    k_map_scatter<<<grid, MAP_THREADS, 0, s>>>(A);
+    if (L.st == 0) k_map_scatter<0><<<grid, MAP_THREADS, 0, s>>>(A);
+    else if (L.st == 1) k_map_scatter<1><<<grid, MAP_THREADS, 0, s>>>(A);
+    else k_map_scatter<2><<<grid, MAP_THREADS, 0, s>>>(A);
 }
 
 }  // namespace lbmdem

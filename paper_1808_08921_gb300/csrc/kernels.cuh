@@ -34,8 +34,9 @@ struct BC {
 // LINK_WARP / 32 chunks of one sphere, each chunk in one direction (one
 // record per lane and chunk):
 //   warp_p[w]    = sphere index
-//   warp_dirs[w] = direction m of chunk k in byte k (the solid neighbour is
-//                  x + c_m), | 128 when the chunk holds a flagged link
+//   chunk_dir[c] = direction m of chunk c (the solid neighbour is x + c_m),
+//                  | 128 when the chunk holds a flagged link; warp w owns
+//                  chunks w LINK_CHUNKS ... (w + 1) LINK_CHUNKS - 1
 //   link[r]      = {cidx of the fluid node x,
 //                   (x - org) + 128 packed 8 bits per axis | maybe << 24 |
 //                   shared << 25 | in_band << 26}
@@ -45,12 +46,14 @@ struct BC {
 // has several candidate spheres (`shared`).  `in_band` marks a fluid node x
 // that may itself be covered before the next re-layout (its fluid bit is
 // read); every other link node stays fluid.  cidx == NONE pads.
-constexpr int LINK_WARP = 128;
+constexpr int LINK_WARP = 256;
+constexpr int LINK_CHUNKS = LINK_WARP / 32;  // chunks per warp
+static_assert(LINK_CHUNKS == 4 || LINK_CHUNKS == 8, "4 or 8 chunk directions per warp");
 
 struct LinkLists {
     const uint2* link;
     const uint32_t* warp_p;
-    const uint32_t* warp_dirs;
+    const uint8_t* chunk_dir;  // LINK_CHUNKS bytes per warp
     uint32_t nwarps;
 };
 

@@ -13,6 +13,43 @@ namespace lbmdem {
 
 static_assert(cx(opp(7)) == -cx(7) && cy(opp(7)) == -cy(7), "opp");
 
+// Four consecutive populations of one plane (the even kernel's vector
+// access): 16 B for FP32, 8 B for the 16-bit forms, streamed (evict-first).
+template <int ST> __device__ __forceinline__ float4 ld4(const typename PopT<ST>::T* p, float fsi);
+template <> __device__ __forceinline__ float4 ld4<0>(const float* p, float) {
+    return __ldcs(reinterpret_cast<const float4*>(p));
+}
+template <> __device__ __forceinline__ float4 ld4<1>(const __nv_bfloat16* p, float fsi) {
+    uint2 r = __ldcs(reinterpret_cast<const uint2*>(p));
+    float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.x));
+    float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.y));
+    return make_float4(a.x * fsi, a.y * fsi, b.x * fsi, b.y * fsi);
+}
+template <> __device__ __forceinline__ float4 ld4<2>(const __half* p, float fsi) {
+    uint2 r = __ldcs(reinterpret_cast<const uint2*>(p));
+    float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+    float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+    return make_float4(a.x * fsi, a.y * fsi, b.x * fsi, b.y * fsi);
+}
+template <int ST> __device__ __forceinline__ void st4(typename PopT<ST>::T* p, float4 v, float fs);
+template <> __device__ __forceinline__ void st4<0>(float* p, float4 v, float) {
+    __stcs(reinterpret_cast<float4*>(p), v);
+}
+template <> __device__ __forceinline__ void st4<1>(__nv_bfloat16* p, float4 v, float fs) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x * fs, v.y * fs), b = __floats2bfloat162_rn(v.z * fs, v.w * fs);
+    uint2 r;
+    r.x = *reinterpret_cast<const uint32_t*>(&a);
+    r.y = *reinterpret_cast<const uint32_t*>(&b);
+    __stcs(reinterpret_cast<uint2*>(p), r);
+}
+template <> __device__ __forceinline__ void st4<2>(__half* p, float4 v, float fs) {
+    __half2 a = __floats2half2_rn(v.x * fs, v.y * fs), b = __floats2half2_rn(v.z * fs, v.w * fs);
+    uint2 r;
+    r.x = *reinterpret_cast<const uint32_t*>(&a);
+    r.y = *reinterpret_cast<const uint32_t*>(&b);
+    __stcs(reinterpret_cast<uint2*>(p), r);
+}
+
 // Eq. 4 with the equilibrium of Eq. 6 and the moments of Eq. 7, on deviations.
 // Returns the moments of the pre-collision state.
 __device__ __forceinline__ void bgk(float g[Q], float tau_inv, float rho_f, float& drho, float& jx,
@@ -116,8 +153,9 @@ __device__ __forceinline__ void mon_flush(const MonAcc& a, const Mon& mon, bool 
 // Even step: node-local.  Each thread owns 4 consecutive compact nodes and
 // moves them with 128-bit loads and stores; solid nodes inside a quad are
 // processed harmlessly (their slots are never read while they are solid).
-template <bool MON>
+template <bool MON, int ST>
 __global__ void __launch_bounds__(256) k_collide_even(Lat L, Mon mon) {
+    auto* f = pops<ST>(L);
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t i0 = t * 4u;
     MonAcc a = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -131,7 +169,7 @@ __global__ void __launch_bounds__(256) k_collide_even(Lat L, Mon mon) {
         float4 v[Q];
 #pragma unroll
         for (int m = 0; m < Q; ++m)
-            v[m] = __ldcs(reinterpret_cast<const float4*>(L.f + (size_t)m * L.nSpad + i0));
+            v[m] = ld4<ST>(f + (size_t)m * L.nSpad + i0, L.fsi);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             float g[Q];
@@ -152,7 +190,7 @@ __global__ void __launch_bounds__(256) k_collide_even(Lat L, Mon mon) {
         }
 #pragma unroll
         for (int m = 0; m < Q; ++m)
-            __stcs(reinterpret_cast<float4*>(L.f + (size_t)m * L.nSpad + i0), v[m]);
+            st4<ST>(f + (size_t)m * L.nSpad + i0, v[m], L.fs);
     }
     mon_flush<MON>(a, mon, true);
 }
@@ -188,8 +226,9 @@ struct LineProbe {
 // its own slot m when x - c_m is solid or outside), collides, and scatters
 // direction m to slot m of x + c_m (or its own slot opp(m)).  Each thread
 // reads and writes the same 19 locations, so the update is in place.
-template <bool MON>
-__global__ void __launch_bounds__(256, 3) k_collide_odd(Lat L, Mon mon) {
+template <bool MON, int ST>
+__global__ void __launch_bounds__(256, 4) k_collide_odd(Lat L, Mon mon) {
+    auto* f = pops<ST>(L);
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     MonAcc a = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     bool active = i < L.nS && fluid_bit(L, i);
@@ -249,20 +288,20 @@ __global__ void __launch_bounds__(256, 3) k_collide_odd(Lat L, Mon mon) {
 #pragma unroll
         for (int m = 0; m < Q - 1; ++m) {
             uint32_t s = nb[opp(m)];
-            g[m] = s != NONE ? L.f[(size_t)opp(m) * L.nSpad + s] : L.f[(size_t)m * L.nSpad + i];
+            g[m] = to_f<ST>(s != NONE ? f[(size_t)opp(m) * L.nSpad + s] : f[(size_t)m * L.nSpad + i], L.fsi);
         }
-        g[18] = L.f[(size_t)18 * L.nSpad + i];
+        g[18] = to_f<ST>(f[(size_t)18 * L.nSpad + i], L.fsi);
         float drho, jx, jy, jz;
         bgk(g, L.tau_inv, L.rho_f, drho, jx, jy, jz);
 #pragma unroll
         for (int m = 0; m < Q - 1; ++m) {
             uint32_t d = nb[m];
             if (d != NONE)
-                L.f[(size_t)m * L.nSpad + d] = g[m];
+                f[(size_t)m * L.nSpad + d] = from_f<ST>(g[m], L.fs);
             else
-                L.f[(size_t)opp(m) * L.nSpad + i] = g[m];
+                f[(size_t)opp(m) * L.nSpad + i] = from_f<ST>(g[m], L.fs);
         }
-        L.f[(size_t)18 * L.nSpad + i] = g[18];
+        f[(size_t)18 * L.nSpad + i] = from_f<ST>(g[18], L.fs);
         if (MON) mon_add(a, drho, jx, jy, jz, L.rho_f);
         if ((i >= mon.pA0 && i < mon.pA1) || (i >= mon.pB0 && i < mon.pB1)) {
             a.pdrho += drho;
@@ -272,21 +311,30 @@ __global__ void __launch_bounds__(256, 3) k_collide_odd(Lat L, Mon mon) {
     mon_flush<MON>(a, mon, true);
 }
 
-void launch_collide(const Lat& L, const Mon& mon, bool odd, bool monitor, cudaStream_t s) {
-    if (L.nS == 0) return;
+template <int ST>
+static void launch_collide_st(const Lat& L, const Mon& mon, bool odd, bool monitor, cudaStream_t s) {
     if (!odd) {
         uint32_t threads = (L.nS + 3) / 4;
         uint32_t blocks = (threads + 255) / 256;
         if (monitor)
-            k_collide_even<true><<<blocks, 256, 0, s>>>(L, mon);
+            k_collide_even<true, ST><<<blocks, 256, 0, s>>>(L, mon);
         else
-            k_collide_even<false><<<blocks, 256, 0, s>>>(L, mon);
+            k_collide_even<false, ST><<<blocks, 256, 0, s>>>(L, mon);
     } else {
         uint32_t blocks = (L.nS + 255) / 256;
         if (monitor)
-            k_collide_odd<true><<<blocks, 256, 0, s>>>(L, mon);
+            k_collide_odd<true, ST><<<blocks, 256, 0, s>>>(L, mon);
         else
-            k_collide_odd<false><<<blocks, 256, 0, s>>>(L, mon);
+            k_collide_odd<false, ST><<<blocks, 256, 0, s>>>(L, mon);
+    }
+}
+
+void launch_collide(const Lat& L, const Mon& mon, bool odd, bool monitor, cudaStream_t s) {
+    if (L.nS == 0) return;
+    switch (L.st) {
+        case 0: launch_collide_st<0>(L, mon, odd, monitor, s); break;
+        case 1: launch_collide_st<1>(L, mon, odd, monitor, s); break;
+        default: launch_collide_st<2>(L, mon, odd, monitor, s); break;
     }
 }
 
@@ -333,8 +381,9 @@ __device__ __forceinline__ void pressure_face(float g[Q], float drho_b, int side
     }
 }
 
-template <bool AFTER_EVEN>
+template <bool AFTER_EVEN, int ST>
 __global__ void k_inlet_outlet(Lat L, BC bc) {
+    auto* f = pops<ST>(L);
     __shared__ float s_drho;
     if (threadIdx.x == 0) s_drho = (float)source_drho(bc.src, *bc.t_dev + 1ull);
     __syncthreads();
@@ -353,27 +402,27 @@ __global__ void k_inlet_outlet(Lat L, BC bc) {
         float g[Q];
 #pragma unroll
         for (int m = 0; m < Q; ++m)
-            if (cx(m) <= 0) g[m] = *pop_loc(L, AFTER_EVEN, x, y, z, i, m);
+            if (cx(m) <= 0) g[m] = to_f<ST>(*pop_loc<ST>(L, AFTER_EVEN, x, y, z, i, m), L.fsi);
         pressure_face(g, s_drho, 0);
 #pragma unroll
         for (int m = 0; m < Q; ++m)
-            if (cx(m) > 0) L.f[(size_t)m * L.nSpad + i] = g[m];  // source outside: own slot
+            if (cx(m) > 0) f[(size_t)m * L.nSpad + i] = from_f<ST>(g[m], L.fs);  // source outside: own slot
     } else if (bc.outlet == 0) {
         bool ufl;
         uint32_t u = stored_index(L, x - 1, y, z, ufl);
         if (!ufl || u == NONE) return;
 #pragma unroll
         for (int m = 0; m < Q; ++m)
-            if (cx(m) < 0) L.f[(size_t)m * L.nSpad + i] = *pop_loc(L, AFTER_EVEN, x - 1, y, z, u, m);
+            if (cx(m) < 0) f[(size_t)m * L.nSpad + i] = *pop_loc<ST>(L, AFTER_EVEN, x - 1, y, z, u, m);
     } else if (bc.outlet == 1) {
         float g[Q];
 #pragma unroll
         for (int m = 0; m < Q; ++m)
-            if (cx(m) >= 0) g[m] = *pop_loc(L, AFTER_EVEN, x, y, z, i, m);
+            if (cx(m) >= 0) g[m] = to_f<ST>(*pop_loc<ST>(L, AFTER_EVEN, x, y, z, i, m), L.fsi);
         pressure_face(g, 0.f, 1);
 #pragma unroll
         for (int m = 0; m < Q; ++m)
-            if (cx(m) < 0) L.f[(size_t)m * L.nSpad + i] = g[m];
+            if (cx(m) < 0) f[(size_t)m * L.nSpad + i] = from_f<ST>(g[m], L.fs);
     }
 }
 
@@ -382,14 +431,22 @@ void launch_inlet_outlet(const Lat& L, const BC& bc, bool after_even, cudaStream
     if (bc.inlet != 0 && bc.outlet > 1) return;
     int n = 2 * L.ny * L.nz;
     int blocks = (n + 127) / 128;
-    if (after_even)
-        k_inlet_outlet<true><<<blocks, 128, 0, s>>>(L, bc);
-    else
-        k_inlet_outlet<false><<<blocks, 128, 0, s>>>(L, bc);
+#define LBMDEM_IO(AE, ST) k_inlet_outlet<AE, ST><<<blocks, 128, 0, s>>>(L, bc)
+    if (after_even) {
+        if (L.st == 0) LBMDEM_IO(true, 0);
+        else if (L.st == 1) LBMDEM_IO(true, 1);
+        else LBMDEM_IO(true, 2);
+    } else {
+        if (L.st == 0) LBMDEM_IO(false, 0);
+        else if (L.st == 1) LBMDEM_IO(false, 1);
+        else LBMDEM_IO(false, 2);
+    }
+#undef LBMDEM_IO
 }
 
 // ------------------------------------------------------------ read-out
 
+template <int ST>
 __global__ void k_read_fields(Lat L, bool after_even, double* rho, double* u, uint8_t* solid) {
     size_t N = (size_t)L.nx * L.ny * L.nz;
     size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -406,7 +463,7 @@ __global__ void k_read_fields(Lat L, bool after_even, double* rho, double* u, ui
     if (fl) {
 #pragma unroll
         for (int m = 0; m < Q; ++m) {
-            double g = (double)*pop_loc(L, after_even, x, y, z, i, m);
+            double g = (double)to_f<ST>(*pop_loc<ST>(L, after_even, x, y, z, i, m), L.fsi);
             d += g;
             jx += cx(m) * g;
             jy += cy(m) * g;
@@ -425,7 +482,10 @@ __global__ void k_read_fields(Lat L, bool after_even, double* rho, double* u, ui
 void launch_read_fields(const Lat& L, bool after_even, double* rho, double* u, uint8_t* solid,
                         cudaStream_t s) {
     size_t N = (size_t)L.nx * L.ny * L.nz;
-    k_read_fields<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(L, after_even, rho, u, solid);
+    unsigned blocks = (unsigned)((N + 255) / 256);
+    if (L.st == 0) k_read_fields<0><<<blocks, 256, 0, s>>>(L, after_even, rho, u, solid);
+    else if (L.st == 1) k_read_fields<1><<<blocks, 256, 0, s>>>(L, after_even, rho, u, solid);
+    else k_read_fields<2><<<blocks, 256, 0, s>>>(L, after_even, rho, u, solid);
 }
 
 }  // namespace lbmdem

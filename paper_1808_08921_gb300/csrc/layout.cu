@@ -204,7 +204,10 @@ __global__ void k_fbits(uint32_t* fbits, uint32_t nA, uint32_t nwords) {
 
 // re-layout: copy the natural populations (state between an odd and an even
 // step: population m of node i sits in slot m of i) into the new order
+template <typename T>
 __global__ void k_gather_old(Lat Lnew, Lat Lold) {
+    T* fn = static_cast<T*>(Lnew.f);
+    const T* fo = static_cast<const T*>(Lold.f);
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Lnew.nA) return;
     int x, y, z;
@@ -213,7 +216,7 @@ __global__ void k_gather_old(Lat Lnew, Lat Lold) {
     uint32_t o = stored_index(Lold, x, y, z, fl);
     if (o == NONE) return;
 #pragma unroll
-    for (int m = 0; m < Q; ++m) Lnew.f[(size_t)m * Lnew.nSpad + i] = Lold.f[(size_t)m * Lold.nSpad + o];
+    for (int m = 0; m < Q; ++m) fn[(size_t)m * Lnew.nSpad + i] = fo[(size_t)m * Lold.nSpad + o];
 }
 
 // band nodes: compact list of (coord) via atomics; candidates found later
@@ -433,7 +436,12 @@ void launch_coords(const LayoutArgs& A, uint32_t nA, uint32_t nSpad, uint32_t* f
 }
 
 void launch_gather_old(const Lat& Lnew, const Lat& Lold, cudaStream_t s) {
-    if (Lnew.nA) k_gather_old<<<(Lnew.nA + 255) / 256, 256, 0, s>>>(Lnew, Lold);
+    if (!Lnew.nA) return;
+    unsigned blocks = (Lnew.nA + 255) / 256;
+    if (Lnew.st == 0)  // the populations move as stored (no conversion)
+        k_gather_old<float><<<blocks, 256, 0, s>>>(Lnew, Lold);
+    else
+        k_gather_old<uint16_t><<<blocks, 256, 0, s>>>(Lnew, Lold);
 }
 
 void launch_band_collect(const LayoutArgs& A, uint32_t* band_coord, uint32_t* count, uint32_t cap,

@@ -17,7 +17,7 @@ from . import build as _build
 SINE, COSINE, STEP, RICKER = 0, 1, 2, 3
 INLET_PRESSURE, X_WALL, X_PERIODIC = 0, 1, 2
 OUT_ZERO_GRAD, OUT_RHO_F, OUT_WALL = 0, 1, 2
-F32 = 0
+F32, BF16_DEV, F16_DEV = 0, 1, 2  # population storage (arithmetic is FP32)
 
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "UNSTABLE", -5: "TIMEOUT",
           -6: "STATE", -7: "CAPACITY", -8: "SKIN", -9: "NO_DEVICE"}
