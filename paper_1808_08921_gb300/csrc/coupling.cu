@@ -135,8 +135,11 @@ template <int ST>
 __global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
     constexpr int K = LINK_CHUNKS;
     auto* f = pops<ST>(L);
-    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w >= B.nwarps) return;  // whole warps
+    // warps in reverse order: the last spheres' nodes were collided last and
+    // are the likeliest to be still in L2
+    const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w0 >= B.nwarps) return;  // whole warps
+    const uint32_t w = B.nwarps - 1 - w0;
     const uint32_t lane = threadIdx.x & 31;
     const int p = (int)B.warp_p[w];
     const unsigned long long dirs = warp_chunk_dirs(B, w);
