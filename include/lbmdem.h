@@ -200,6 +200,40 @@ int lbm_dem_read_counters(lbmdem_ctx* c, int64_t out[10]);
 int lbm_dem_set_timing(lbmdem_ctx* c, int32_t enable);
 int lbm_dem_read_timing(lbmdem_ctx* c, double ms[5], int64_t launches[5]);
 
+/* ---- Batched columns ------------------------------------------------------
+ * The paper's study of the acoustic source (Section 4.4: input waveforms and
+ * frequencies of Table 2) runs one column per source; a batch advances many
+ * such independent contexts (columns of any length, packing and source)
+ * together.  For each
+ * chunk of 16 steps one CUDA graph holds every active column's step kernels
+ * as parallel branches, launched once on the batch's own stream.  Columns may
+ * take different step counts; a column with fewer than 16 steps left
+ * finishes alone through lbm_dem_step.  Per-kernel timing is not recorded for
+ * steps taken inside the batch graph.  The contexts stay owned by the caller
+ * and must outlive the batch; use no context elsewhere while a batch call
+ * runs. */
+typedef struct lbmdem_batch lbmdem_batch; /* opaque, library-owned */
+
+/* Group n contexts (distinct, all on one device, each after set_packing).
+ * Errors: INVALID_ARG (NULL, duplicates, mixed devices), STATE, CUDA. */
+int lbm_dem_batch_create(lbmdem_ctx* const* cols, int32_t n, lbmdem_batch** out);
+
+/* Advance column i by steps[i] >= 0 coupled steps (asynchronous like
+ * lbm_dem_step; re-layout checks of mobile columns read a few bytes back
+ * between chunks).  Errors: INVALID_ARG, a column's latched status, CUDA. */
+int lbm_dem_batch_step(lbmdem_batch* b, const int64_t* steps);
+
+/* Wait for the batch and every column; returns the first column status. */
+int lbm_dem_batch_sync(lbmdem_batch* b);
+
+/* Graph launches issued by lbm_dem_batch_step so far (-1 for NULL). */
+int64_t lbm_dem_batch_graph_launches(const lbmdem_batch* b);
+
+const char* lbm_dem_batch_last_error(const lbmdem_batch* b);
+
+/* Release the batch's stream, events and graph (not the contexts). */
+void lbm_dem_batch_destroy(lbmdem_batch* b);
+
 /* One-line description of the last error on this context ("" if none). */
 const char* lbm_dem_last_error(const lbmdem_ctx* c);
 

@@ -1000,6 +1000,212 @@ int lbm_dem_step(lbmdem_ctx* c, int64_t n) {
     return 0;
 }
 
+// ------------------------------------------------------------ batched columns
+
+}  // extern "C"
+
+// A batch advances several independent contexts (columns) of one device
+// together: for each chunk of BATCH_CHUNK steps one CUDA graph holds every
+// active column's kernels as parallel branches (each column's kernels on its
+// own stream, joined on the batch stream), so the small kernels of many
+// columns share the GPU and one graph launch replaces hundreds of kernel
+// launches.  Columns may ask for different step counts; a column leaves the
+// graph when fewer than BATCH_CHUNK of its steps remain and finishes through
+// lbm_dem_step.  Re-layout checks of mobile columns happen between chunks.
+struct lbmdem_batch {
+    std::vector<lbmdem_ctx*> cols;
+    int device = 0;
+    cudaStream_t master = nullptr;
+    cudaEvent_t fork = nullptr, done = nullptr;
+    std::vector<cudaEvent_t> join, pre;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<int> gcols;           // columns in the captured graph
+    std::vector<int64_t> glaunch;     // kernels per column in one graph launch
+    int64_t graph_launches = 0;       // graph launches so far
+    std::string err;
+};
+
+namespace {
+constexpr int BATCH_CHUNK = 16;
+
+int bfail(lbmdem_batch* b, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    return code;
+}
+
+#define BCK(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return bfail(b, LBMDEM_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
+                         __FILE__, __LINE__);                                                      \
+    } while (0)
+
+void batch_destroy_graph(lbmdem_batch* b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->gcols.clear();
+}
+
+int batch_capture(lbmdem_batch* b, const std::vector<int>& act) {
+    batch_destroy_graph(b);
+    BCK(cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal));
+    cudaEventRecord(b->fork, b->master);
+    b->glaunch.assign(b->cols.size(), 0);
+    for (int i : act) {
+        lbmdem_ctx* c = b->cols[i];
+        cudaStreamWaitEvent(c->stream, b->fork, 0);
+        bool tm = c->timing;
+        c->timing = false;  // per-kernel timing is not recorded inside a batch
+        int64_t l0 = c->launches;
+        bool mon = c->p.monitor_every > 0;
+        for (int k = 0; k < BATCH_CHUNK; ++k) enqueue_step(c, k & 1, mon && k == BATCH_CHUNK - 1);
+        b->glaunch[i] = c->launches - l0;
+        c->launches = l0;
+        c->timing = tm;
+        cudaEventRecord(b->join[i], c->stream);
+        cudaStreamWaitEvent(b->master, b->join[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->master, &g);
+    if (e != cudaSuccess) return bfail(b, LBMDEM_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, LBMDEM_ERR_CUDA, "batch instantiate: %s", cudaGetErrorString(e));
+    b->gcols = act;
+    return 0;
+}
+}  // namespace
+
+extern "C" {
+
+int lbm_dem_batch_create(lbmdem_ctx* const* cols, int32_t n, lbmdem_batch** out) {
+    if (!out) return LBMDEM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!cols || n <= 0) return LBMDEM_ERR_INVALID_ARG;
+    int dev = -1;
+    for (int i = 0; i < n; ++i) {
+        if (!cols[i]) return LBMDEM_ERR_INVALID_ARG;
+        if (!cols[i]->have_packing) return LBMDEM_ERR_STATE;
+        for (int j = 0; j < i; ++j)
+            if (cols[j] == cols[i]) return LBMDEM_ERR_INVALID_ARG;
+        if (dev >= 0 && cols[i]->p.device != dev) return LBMDEM_ERR_INVALID_ARG;
+        dev = cols[i]->p.device;
+    }
+    lbmdem_batch* b = new lbmdem_batch();
+    b->cols.assign(cols, cols + n);
+    b->device = dev;
+    if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&b->master, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+        lbm_dem_batch_destroy(b);
+        return LBMDEM_ERR_CUDA;
+    }
+    b->join.resize(n, nullptr);
+    b->pre.resize(n, nullptr);
+    for (int i = 0; i < n; ++i)
+        if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->pre[i], cudaEventDisableTiming) != cudaSuccess) {
+            lbm_dem_batch_destroy(b);
+            return LBMDEM_ERR_CUDA;
+        }
+    *out = b;
+    return 0;
+}
+
+int lbm_dem_batch_step(lbmdem_batch* b, const int64_t* steps) {
+    if (!b || !steps) return LBMDEM_ERR_INVALID_ARG;
+    const int n = (int)b->cols.size();
+    BCK(cudaSetDevice(b->device));
+    std::vector<int64_t> rem(steps, steps + n);
+    for (int i = 0; i < n; ++i) {
+        lbmdem_ctx* c = b->cols[i];
+        if (rem[i] < 0) return bfail(b, LBMDEM_ERR_INVALID_ARG, "steps[%d] < 0", i);
+        if (c->status_latched)
+            return bfail(b, c->status_latched, "column %d: %s", i, status_text(c->status_latched));
+        if (int r = ensure_probe(c, c->t + rem[i] + 1)) return bfail(b, r, "column %d: %s", i, c->err.c_str());
+    }
+    for (;;) {
+        // host-side work of each column between graph launches: re-layout
+        // checks, and single steps to reach an even step count
+        std::vector<int> act;
+        for (int i = 0; i < n; ++i) {
+            lbmdem_ctx* c = b->cols[i];
+            if (rem[i] <= 0) continue;
+            if (c->any_mobile && c->steps_until_check <= 0) {
+                bool did;
+                if (int r = check_and_relayout(c, did)) return bfail(b, r, "column %d: %s", i, c->err.c_str());
+            }
+            if (c->t % 2) {
+                if (int r = lbm_dem_step(c, 1)) return bfail(b, r, "column %d: %s", i, c->err.c_str());
+                rem[i] -= 1;
+            }
+            int64_t room = c->any_mobile ? c->steps_until_check : rem[i];
+            if (rem[i] >= BATCH_CHUNK && room >= BATCH_CHUNK && c->t % 2 == 0) act.push_back(i);
+        }
+        if (act.empty()) break;
+        if (act != b->gcols || !b->gexec) {
+            if (int r = batch_capture(b, act)) return r;
+        }
+        for (int i : act) {  // the graph runs after each column's earlier work
+            BCK(cudaEventRecord(b->pre[i], b->cols[i]->stream));
+            BCK(cudaStreamWaitEvent(b->master, b->pre[i], 0));
+        }
+        BCK(cudaGraphLaunch(b->gexec, b->master));
+        b->graph_launches += 1;
+        BCK(cudaEventRecord(b->done, b->master));
+        for (int i : act) {  // and before each column's later work
+            lbmdem_ctx* c = b->cols[i];
+            BCK(cudaStreamWaitEvent(c->stream, b->done, 0));
+            c->launches += b->glaunch[i];
+            if (c->p.monitor_every > 0) c->mon_step = c->t + BATCH_CHUNK - 1;
+            c->t += BATCH_CHUNK;
+            c->steps_until_check -= BATCH_CHUNK;
+            rem[i] -= BATCH_CHUNK;
+        }
+    }
+    for (int i = 0; i < n; ++i) {  // what is left: fewer than a chunk per column
+        if (rem[i] <= 0) continue;
+        if (int r = lbm_dem_step(b->cols[i], rem[i])) return bfail(b, r, "column %d: %s", i, b->cols[i]->err.c_str());
+    }
+    return 0;
+}
+
+int lbm_dem_batch_sync(lbmdem_batch* b) {
+    if (!b) return LBMDEM_ERR_INVALID_ARG;
+    BCK(cudaSetDevice(b->device));
+    BCK(cudaStreamSynchronize(b->master));
+    for (lbmdem_ctx* c : b->cols) {
+        int r = lbm_dem_status(c);
+        if (r) return bfail(b, r, "%s", c->err.c_str());
+    }
+    return 0;
+}
+
+int64_t lbm_dem_batch_graph_launches(const lbmdem_batch* b) { return b ? b->graph_launches : -1; }
+
+const char* lbm_dem_batch_last_error(const lbmdem_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void lbm_dem_batch_destroy(lbmdem_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->master) cudaStreamSynchronize(b->master);
+    batch_destroy_graph(b);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->pre)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->master) cudaStreamDestroy(b->master);
+    delete b;
+}
+
 int lbm_dem_relayout(lbmdem_ctx* c) {
     if (!c) return LBMDEM_ERR_INVALID_ARG;
     if (!c->have_packing) return fail(c, LBMDEM_ERR_STATE, "relayout before set_packing");

@@ -28,7 +28,9 @@ SYMBOLS = ("lbm_dem_default_params", "lbm_dem_init", "lbm_dem_set_packing",
            "lbm_dem_read_fields", "lbm_dem_read_particles", "lbm_dem_read_particles_noalloc",
            "lbm_dem_read_probe",
            "lbm_dem_read_monitors", "lbm_dem_read_counters", "lbm_dem_set_timing",
-           "lbm_dem_read_timing", "lbm_dem_last_error", "lbm_dem_destroy")
+           "lbm_dem_read_timing", "lbm_dem_last_error", "lbm_dem_destroy",
+           "lbm_dem_batch_create", "lbm_dem_batch_step", "lbm_dem_batch_sync",
+           "lbm_dem_batch_graph_launches", "lbm_dem_batch_last_error", "lbm_dem_batch_destroy")
 
 
 class Params(C.Structure):
@@ -90,6 +92,15 @@ def load(build_if_missing: bool = True):
     lib.lbm_dem_last_error.restype = C.c_char_p
     lib.lbm_dem_destroy.argtypes = [vp]
     lib.lbm_dem_destroy.restype = None
+    lib.lbm_dem_batch_create.argtypes = [P(vp), i32, P(vp)]
+    lib.lbm_dem_batch_step.argtypes = [vp, P(i64)]
+    lib.lbm_dem_batch_sync.argtypes = [vp]
+    lib.lbm_dem_batch_graph_launches.argtypes = [vp]
+    lib.lbm_dem_batch_graph_launches.restype = i64
+    lib.lbm_dem_batch_last_error.argtypes = [vp]
+    lib.lbm_dem_batch_last_error.restype = C.c_char_p
+    lib.lbm_dem_batch_destroy.argtypes = [vp]
+    lib.lbm_dem_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -233,6 +244,52 @@ class Sim:
     def close(self):
         if getattr(self, "_h", None):
             load().lbm_dem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several Sim columns advanced together (lbm_dem_batch_*): one CUDA graph
+    per 16-step chunk holds every active column's kernels."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        arr = (C.c_void_p * len(self.sims))(*[s._h for s in self.sims])
+        h = C.c_void_p()
+        rc = load().lbm_dem_batch_create(arr, len(self.sims), C.byref(h))
+        if rc != 0:
+            raise LbmDemError(rc, "lbm_dem_batch_create")
+        self._h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            msg = load().lbm_dem_batch_last_error(self._h)
+            raise LbmDemError(rc, msg.decode() if msg else "")
+        return rc
+
+    def step(self, steps):
+        """Advance column i by steps[i] steps (an int applies to every column)."""
+        if np.isscalar(steps):
+            steps = [int(steps)] * len(self.sims)
+        arr = np.ascontiguousarray(steps, np.int64)
+        assert arr.shape == (len(self.sims),)
+        self._check(load().lbm_dem_batch_step(self._h, arr.ctypes.data_as(C.POINTER(C.c_int64))))
+
+    def sync(self):
+        self._check(load().lbm_dem_batch_sync(self._h))
+
+    @property
+    def graph_launches(self):
+        return int(load().lbm_dem_batch_graph_launches(self._h))
+
+    def close(self):
+        if self._h:
+            load().lbm_dem_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

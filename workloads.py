@@ -178,3 +178,31 @@ def random_small(seed: int, nx=20, ny=12, nz=12, n=4, R=2.5, tau=0.7,
     return Workload(name=f"rand{seed}", nx=nx, ny=ny, nz=nz, tau=tau, X=X,
                     R=np.full(m, R), fixed=fixed, V=V, W=W, steps=steps,
                     dem_substeps=4)
+
+
+def config_sweep(n: int = 48, seed: int = 4, amplitude: float = 1e-3):
+    """Source sweep of independent columns: cross-section 32 x 32, lengths
+    drawn uniformly from the multiples of 16 in [256, 1024], FCC a = 16 with
+    R = 5.7 (the 16 x 16 x 128 column's physics, tau 0.8).  The first
+    n - n // 6 columns carry sine sources with periods log-spaced from 50 to
+    800 steps, the rest Ricker pulses over the same periods.  Each column
+    runs until its front reaches the outlet, ceil(L sqrt(3)) steps.
+
+    Returns (workloads, steps)."""
+    rng = np.random.default_rng(seed)
+    lengths = 16 * rng.integers(16, 65, size=n)
+    n_ricker = n // 6
+    n_sine = n - n_ricker
+    periods = list(np.geomspace(50, 800, n_sine)) + list(np.geomspace(50, 800, max(n_ricker, 1)))[:n_ricker]
+    ws, steps = [], []
+    for k in range(n):
+        L = int(lengths[k])
+        w = fcc_column(L, 32, 32, 0.8, 16.0, 5.7, jitter=0.01, seed=seed * 1000 + k,
+                       period=float(periods[k]), amplitude=amplitude, mu=0.3, substeps=10,
+                       name=f"sweep{k}_32x32x{L}")
+        if k >= n_sine:
+            w.waveform = RICKER
+            w.t0 = float(periods[k])  # one period of the peak frequency
+        ws.append(w)
+        steps.append(int(math.ceil(L * math.sqrt(3.0))))
+    return ws, steps
