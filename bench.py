@@ -362,6 +362,60 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_sweep(args):
+    """The source sweep: 48 independent columns 32 x 32 x L (L 256..1024, sine
+    and Ricker sources, ceil(L sqrt 3) steps each).  The autotuner picks the
+    DEM subcycle and the collide+stream tile on the median column; the
+    columns then run as one batch (one CUDA graph per 16-step chunk) and, for
+    comparison, one after another.  value = fluid-node updates of all columns
+    per second of the batched run."""
+    import torch
+
+    import workloads
+    from paper_1808_08921_gb300 import autotune, lbmdem
+
+    ws, steps = workloads.config_sweep(48)
+    med = sorted(range(len(ws)), key=lambda k: ws[k].nx)[len(ws) // 2]
+    over = dict(skin=0.25, dem_skin=0.5)
+    tuned = autotune.tune(ws[med], steps=96, **over) if not args.no_tune else {"dem_substeps": 10, "tile": 256}
+    over.update(dem_substeps=tuned["dem_substeps"], tile=tuned["tile"])
+    out = {}
+    for mode in ("batch", "sequential"):
+        sims = [lbmdem.Sim.from_workload(w, **over) for w in ws]
+        fluid = [s.counters()["fluid"] for s in sims]
+        torch.cuda.synchronize()
+        with Clocks(0) as clk:
+            t0 = time.perf_counter()
+            if mode == "batch":
+                b = lbmdem.Batch(sims)
+                b.step(steps)
+                b.sync()
+                gl = b.graph_launches
+                b.close()
+            else:
+                for s, k in zip(sims, steps):
+                    s.step(k)
+                for s in sims:
+                    s.status()
+                gl = 0
+            dt = time.perf_counter() - t0
+        st = max(abs(s.status()) for s in sims)
+        upd = sum(f * k for f, k in zip(fluid, steps))
+        out[mode] = {"s": round(dt, 3), "mlups": round(upd / dt / 1e6, 1), "graph_launches": gl, "status": st,
+                     "clocks": clk.summary()}
+        for s in sims:
+            s.close()
+    line = {"metric": "source sweep MLUPS (fluid nodes, 48 columns)", "value": out["batch"]["mlups"], "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sweep48_32x32xL_a16_R5.7_tau0.8", "columns": len(ws),
+                       "lengths": [w.nx for w in ws], "steps": steps, "fluid_updates": upd,
+                       "dem_substeps": over["dem_substeps"], "tile": over["tile"]},
+            "batch": out["batch"], "sequential": out["sequential"],
+            "speedup_vs_sequential": round(out["batch"]["mlups"] / max(out["sequential"]["mlups"], 1e-9), 3),
+            "autotune": tuned}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,6 +424,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
                     help="population storage (deviations; the arithmetic is FP32 in every case)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="the 48-column source sweep (batched, autotuned) instead of the single column")
+    ap.add_argument("--no-tune", action="store_true", help="sweep without the autotuner (K = 10, tile 256)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -379,6 +436,9 @@ def main():
         args.steps = 20 if args.steps is None else args.steps
         args.warmup = 3 if args.warmup is None else args.warmup
         run_reference(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     args.steps = 2000 if args.steps is None else args.steps
     args.warmup = 200 if args.warmup is None else args.warmup

@@ -570,7 +570,7 @@ static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
             cudaMemsetAsync(&sd->max_u_bits, 0, sizeof(uint32_t), s);
         }
         if (tm) record_pair_begin(c, 0, e);
-        launch_collide(L, mon, parity == 1, monitor, s);
+        launch_collide(L, mon, parity == 1, monitor, c->p.tile > 0 ? c->p.tile : 256, s);
         if (tm) record_pair_end(c, e);
         LinkLists LL{c->surf_link.p, c->warp_p.p, c->chunk_dir.p, c->nwarps};
         if (tm) record_pair_begin(c, 1, e);
@@ -717,6 +717,7 @@ void lbm_dem_default_params(lbmdem_params* p) {
     p->monitor_every = 0;
     p->graph_steps = 0;
     p->max_flips = 0;
+    p->tile = 0;
     p->device = 0;
     p->cuda_stream = nullptr;
 }
@@ -737,6 +738,7 @@ int lbm_dem_init(const lbmdem_params* pp, lbmdem_ctx** out) {
     if (p.probe_x >= p.nx || p.probe_x < -1) return LBMDEM_ERR_INVALID_ARG;
     if (!(p.E_p > 0) || !(p.nu_p > -1 && p.nu_p < 0.5) || !(p.mu >= 0) || !(p.rho_p > 0))
         return LBMDEM_ERR_INVALID_ARG;
+    if (p.tile != 0 && p.tile != 64 && p.tile != 128 && p.tile != 256) return LBMDEM_ERR_INVALID_ARG;
     if (p.skin < 0 || p.dem_skin < 0 || p.graph_steps < 0 || p.graph_steps % 2 || p.max_flips < 0)
         return LBMDEM_ERR_INVALID_ARG;
     int ndev = 0;

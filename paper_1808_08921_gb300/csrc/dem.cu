@@ -512,11 +512,13 @@ void launch_dem_step(const Dem& D, bool init_only, cudaStream_t s) {
     cfg.numAttrs = 1;
     int cmax = dev >= 0 && dev < 64 ? g_dsm_cluster[dev] : 0;
     if (!init_only && cmax > 0 && need <= (long long)cmax * DSM_THREADS) {
-        int C = 1, T = (int)(((need + 31) / 32) * 32);
-        if (need > DSM_THREADS) {
-            C = (int)((need + DSM_THREADS - 1) / DSM_THREADS);
-            T = DSM_THREADS;
-        }
+        // the smallest CTAs that fit the cluster: a CTA holds half an SM's
+        // registers at 256 threads, so DEM clusters of concurrent columns
+        // (batches) find room next to the lattice kernels
+        int T = need <= (long long)cmax * (DSM_THREADS / 2) ? DSM_THREADS / 2 : DSM_THREADS;
+        int C = 1;
+        if (need > T) C = (int)((need + T - 1) / T);
+        else T = (int)(((need + 31) / 32) * 32);
         cfg.gridDim = dim3(C, 1, 1);
         cfg.blockDim = dim3(T, 1, 1);
         cfg.dynamicSmemBytes = 6 * (T / TEAM) * sizeof(float4);

@@ -312,29 +312,30 @@ __global__ void __launch_bounds__(256, 4) k_collide_odd(Lat L, Mon mon) {
 }
 
 template <int ST>
-static void launch_collide_st(const Lat& L, const Mon& mon, bool odd, bool monitor, cudaStream_t s) {
+static void launch_collide_st(const Lat& L, const Mon& mon, bool odd, bool monitor, int tile, cudaStream_t s) {
     if (!odd) {
         uint32_t threads = (L.nS + 3) / 4;
-        uint32_t blocks = (threads + 255) / 256;
+        uint32_t blocks = (threads + tile - 1) / tile;
         if (monitor)
-            k_collide_even<true, ST><<<blocks, 256, 0, s>>>(L, mon);
+            k_collide_even<true, ST><<<blocks, tile, 0, s>>>(L, mon);
         else
-            k_collide_even<false, ST><<<blocks, 256, 0, s>>>(L, mon);
+            k_collide_even<false, ST><<<blocks, tile, 0, s>>>(L, mon);
     } else {
-        uint32_t blocks = (L.nS + 255) / 256;
+        uint32_t blocks = (L.nS + tile - 1) / tile;
         if (monitor)
-            k_collide_odd<true, ST><<<blocks, 256, 0, s>>>(L, mon);
+            k_collide_odd<true, ST><<<blocks, tile, 0, s>>>(L, mon);
         else
-            k_collide_odd<false, ST><<<blocks, 256, 0, s>>>(L, mon);
+            k_collide_odd<false, ST><<<blocks, tile, 0, s>>>(L, mon);
     }
 }
 
-void launch_collide(const Lat& L, const Mon& mon, bool odd, bool monitor, cudaStream_t s) {
+// tile: threads per block (64, 128 or 256; the kernels are bounded for 256)
+void launch_collide(const Lat& L, const Mon& mon, bool odd, bool monitor, int tile, cudaStream_t s) {
     if (L.nS == 0) return;
     switch (L.st) {
-        case 0: launch_collide_st<0>(L, mon, odd, monitor, s); break;
-        case 1: launch_collide_st<1>(L, mon, odd, monitor, s); break;
-        default: launch_collide_st<2>(L, mon, odd, monitor, s); break;
+        case 0: launch_collide_st<0>(L, mon, odd, monitor, tile, s); break;
+        case 1: launch_collide_st<1>(L, mon, odd, monitor, tile, s); break;
+        default: launch_collide_st<2>(L, mon, odd, monitor, tile, s); break;
     }
 }
 

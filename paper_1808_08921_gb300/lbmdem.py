@@ -44,7 +44,7 @@ class Params(C.Structure):
                 ("probe_x", C.c_int32), ("lbm_on", C.c_int32),
                 ("skin", C.c_double), ("dem_skin", C.c_double),
                 ("monitor_every", C.c_int32), ("graph_steps", C.c_int32),
-                ("max_flips", C.c_int32), ("device", C.c_int32),
+                ("max_flips", C.c_int32), ("tile", C.c_int32), ("device", C.c_int32),
                 ("cuda_stream", C.c_void_p)]
 
 

@@ -43,7 +43,7 @@ int main(void) {
   printf("size %zu\n", sizeof(lbmdem_params));
   O(nx) O(ny) O(nz) O(tau) O(rho_f) O(storage) O(inlet) O(outlet) O(dem_substeps)
   O(E_p) O(nu_p) O(mu) O(rho_p) O(body_force) O(probe_x) O(lbm_on) O(skin) O(dem_skin)
-  O(monitor_every) O(graph_steps) O(max_flips) O(device) O(cuda_stream)
+  O(monitor_every) O(graph_steps) O(max_flips) O(tile) O(device) O(cuda_stream)
   return 0;
 }
 """
