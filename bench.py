@@ -416,6 +416,64 @@ def run_sweep(args):
     print(json.dumps(line))
 
 
+def run_adjoint(args):
+    """Gradient of the probe-plane pressure misfit on the fixed 64 x 64 x 512
+    packing (256 spheres R 11.4, probe x = 400, 5000 steps, checkpoints every
+    100): the adjoint's cost against the plain forward run, and its gradient
+    against central finite differences of the forward loss."""
+    import numpy as np
+
+    import workloads
+    from paper_1808_08921_gb300 import adjoint, lbmdem
+
+    steps, every = args.adj_steps, 100
+    w = workloads.config_adjoint(steps)
+    tau, amp = w.tau, w.amplitude
+
+    def sim(t, a):
+        s = lbmdem.Sim(lbmdem.params_from_workload(w, tau=t))
+        s.set_pressure_source(w.waveform, a, w.omega, w.t_n, w.t0)
+        s.set_packing(w.X, w.R, None, None, w.fixed)
+        return s
+
+    # target: the forward trace at (tau, amp) with a seeded N(0, 1e-5 rho_f c_s^2) perturbation
+    s = sim(tau, amp)
+    s.step(steps)
+    base = s.probe()[:steps] / 3.0
+    s.close()
+    target = base + np.random.default_rng(7).normal(0.0, 1e-5 / 3.0, steps)
+
+    def forward_loss(t, a):
+        s = sim(t, a)
+        s.status()
+        t0 = time.perf_counter()
+        s.step(steps)
+        s.status()
+        dt = time.perf_counter() - t0
+        p = s.probe()[:steps] / 3.0
+        s.close()
+        return float(((p - target) ** 2).sum()), dt
+
+    L0, t_fwd = forward_loss(tau, amp)
+    s = sim(tau, amp)
+    s.status()
+    t0 = time.perf_counter()
+    L, d_tau, d_amp, _ = s.adjoint(steps, every, target)
+    t_adj = time.perf_counter() - t0
+    s.close()
+    h, ha = 1e-3 * tau, 1e-2 * amp
+    fd_tau = (forward_loss(tau + h, amp)[0] - forward_loss(tau - h, amp)[0]) / (2 * h)
+    fd_amp = (forward_loss(tau, amp + ha)[0] - forward_loss(tau, amp - ha)[0]) / (2 * ha)
+    line = {"metric": "adjoint cost / forward cost", "value": round(t_adj / t_fwd, 3), "unit": "ratio",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "lattice": [w.nx, w.ny, w.nz], "spheres": len(w.R), "steps": steps,
+                       "checkpoint_every": every, "probe_x": w.probe_x, "tau": tau, "amplitude": amp},
+            "forward_s": round(t_fwd, 4), "adjoint_s": round(t_adj, 4), "loss": L, "loss_forward": L0,
+            "dL_dtau": d_tau, "fd_dL_dtau": fd_tau, "rel_err_tau": abs(d_tau - fd_tau) / max(abs(fd_tau), 1e-300),
+            "dL_damp": d_amp, "fd_dL_damp": fd_amp, "rel_err_amp": abs(d_amp - fd_amp) / max(abs(fd_amp), 1e-300)}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -427,6 +485,9 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="the 48-column source sweep (batched, autotuned) instead of the single column")
     ap.add_argument("--no-tune", action="store_true", help="sweep without the autotuner (K = 10, tile 256)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="the adjoint's cost and gradient check on the fixed 64 x 64 x 512 packing")
+    ap.add_argument("--adj-steps", type=int, default=5000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -439,6 +500,9 @@ def main():
         return
     if args.sweep:
         run_sweep(args)
+        return
+    if args.adjoint:
+        run_adjoint(args)
         return
     args.steps = 2000 if args.steps is None else args.steps
     args.warmup = 200 if args.warmup is None else args.warmup

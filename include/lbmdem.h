@@ -201,6 +201,22 @@ int lbm_dem_read_counters(lbmdem_ctx* c, int64_t out[10]);
 int lbm_dem_set_timing(lbmdem_ctx* c, int32_t enable);
 int lbm_dem_read_timing(lbmdem_ctx* c, double ms[5], int64_t launches[5]);
 
+/* Gradient of the probe-plane pressure misfit for a fixed packing (every
+ * sphere fixed; the paper's pressure p = c_s^2 rho, Section 3, at the probe
+ * plane of Section 3.2): runs `steps` coupled steps from the current state
+ * (t even), L = sum_k (p(k) - target[k])^2 over the probe trace entries
+ * p(k) = c_s^2 * trace[t0 + k], k = 0 .. steps-1, and the exact gradient of
+ * that discrete L with respect to tau (Eq. 4) and the source amplitude rho'
+ * (Eq. 25) by the adjoint of the step (hand-written reverse kernels), with
+ * the populations checkpointed every `every` (even) steps and each segment
+ * recomputed once.  Writes *loss, *dL_dtau, *dL_damp and, if not NULL,
+ * trace_out[steps] = p(k).  Leaves the context at t0 + steps.  Device memory:
+ * the checkpoints (steps / every population copies) and `every` FP32
+ * snapshots.  Errors: INVALID_ARG, STATE (mobile spheres, no probe, odd t),
+ * OOM, CUDA. */
+int lbm_dem_adjoint(lbmdem_ctx* c, int64_t steps, int32_t every, const double* target, double* loss,
+                    double* dL_dtau, double* dL_damp, double* trace_out);
+
 /* ---- Batched columns ------------------------------------------------------
  * The paper's study of the acoustic source (Section 4.4: input waveforms and
  * frequencies of Table 2) runs one column per source; a batch advances many

@@ -139,6 +139,7 @@ struct lbmdem_ctx {
     int64_t relayouts = 0;
     int64_t steps_until_check = 0;
     bool capturing = false;      // inside stream capture (events become graph nodes)
+    bool suppress_probe = false; // re-running steps whose probe trace is recorded
     int64_t launches = 0;        // kernels enqueued by the step loop
     int64_t glaunches = 0;       // kernels in one captured graph
 };
@@ -559,7 +560,7 @@ static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
         mon.acc = sd->mon;
         mon.umax_bits = &sd->max_u_bits;
         mon.status = &sd->status;
-        mon.probe_sum = c->p.probe_x >= 0 ? c->probe.p : nullptr;
+        mon.probe_sum = c->p.probe_x >= 0 && !c->suppress_probe ? c->probe.p : nullptr;
         mon.t_dev = &sd->t;
         mon.pA0 = c->pA0;
         mon.pA1 = c->pA1;
@@ -1206,6 +1207,136 @@ void lbm_dem_batch_destroy(lbmdem_batch* b) {
     if (b->done) cudaEventDestroy(b->done);
     if (b->master) cudaStreamDestroy(b->master);
     delete b;
+}
+
+// ------------------------------------------------------------ adjoint
+
+}  // extern "C"
+
+namespace {
+// shape(t) of the source, rho_in = rho_f + amplitude * shape(t) (Eq. 25,
+// Table 2; Ricker: a = pi f (t - t0), f = omega / 2 pi)
+double source_shape(const Source& S, int64_t t) {
+    if (S.t_n >= 0 && t > S.t_n) return 0.0;
+    double ph = S.omega * (double)t;
+    switch (S.waveform) {
+        case LBMDEM_SINE: return std::sin(ph);
+        case LBMDEM_COSINE: return 1.0 - std::cos(ph);
+        case LBMDEM_STEP: return 1.0;
+        case LBMDEM_RICKER: {
+            double a = 0.5 * S.omega * ((double)t - S.t0);
+            return (1.0 - 2.0 * a * a) * std::exp(-a * a);
+        }
+    }
+    return 0.0;
+}
+}  // namespace
+
+extern "C" {
+
+int lbm_dem_adjoint(lbmdem_ctx* c, int64_t steps, int32_t every, const double* target, double* loss,
+                    double* dL_dtau, double* dL_damp, double* trace_out) {
+    if (!c || steps <= 0 || !target || every < 2 || every % 2) return fail(c, LBMDEM_ERR_INVALID_ARG, "adjoint: arguments");
+    if (!c->have_packing || !c->lbm) return fail(c, LBMDEM_ERR_STATE, "adjoint: needs a packing and the fluid");
+    if (c->any_mobile) return fail(c, LBMDEM_ERR_STATE, "adjoint: every sphere must be fixed");
+    if (c->p.probe_x < 0) return fail(c, LBMDEM_ERR_STATE, "adjoint: no probe plane");
+    if (c->t % 2) return fail(c, LBMDEM_ERR_STATE, "adjoint: needs an even step count");
+    if (c->status_latched) return fail(c, c->status_latched, "%s", status_text(c->status_latched));
+    CK(cudaSetDevice(c->p.device));
+    cudaStream_t s = c->stream;
+    const int64_t t0 = c->t;
+    const size_t esz = c->p.storage == LBMDEM_F32 ? 4 : 2;
+    const size_t fbytes = (size_t)Q * c->nSpad * esz;
+    const int64_t nseg = (steps + every - 1) / every;
+    // forward with a checkpoint of the populations at the start of every segment
+    DBuf<uint8_t> ck;
+    CK(ck.alloc(fbytes * (size_t)nseg));
+    for (int64_t g = 0; g < nseg; ++g) {
+        CK(cudaMemcpyAsync(ck.p + fbytes * g, c->f.p, fbytes, cudaMemcpyDeviceToDevice, s));
+        int64_t n = std::min<int64_t>(every, steps - g * every);
+        if (int r = lbm_dem_step(c, n)) return r;
+    }
+    std::vector<double> trace((size_t)(t0 + steps));
+    int64_t len = 0;
+    if (int r = lbm_dem_read_probe(c, trace.data(), t0 + steps, &len)) return r;
+    // loss and its derivative: p = c_s^2 rho (probe-plane mean)
+    const double cs2 = 1.0 / 3.0;
+    std::vector<double> dl((size_t)steps);
+    double L = 0.0;
+    for (int64_t k = 0; k < steps; ++k) {
+        double p = cs2 * trace[(size_t)(t0 + k)], e = p - target[k];
+        L += e * e;
+        dl[(size_t)k] = 2.0 * e;
+        if (trace_out) trace_out[k] = p;
+    }
+    // probe-plane fluid nodes (static: every sphere is fixed)
+    int64_t np_plane = 0;
+    {
+        std::vector<uint32_t> fb(c->nSpad / 32), coord(c->nSpad);
+        CK(cudaMemcpy(fb.data(), c->fbits.p, sizeof(uint32_t) * fb.size(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(coord.data(), c->coord.p, sizeof(uint32_t) * coord.size(), cudaMemcpyDeviceToHost));
+        for (uint32_t i = 0; i < c->nS; ++i)
+            if ((fb[i >> 5] >> (i & 31) & 1u) && (int)(coord[i] >> 20) == c->p.probe_x) ++np_plane;
+    }
+    if (np_plane == 0) return fail(c, LBMDEM_ERR_STATE, "adjoint: probe plane without fluid");
+    // backward: recompute each segment from its checkpoint, keeping the
+    // natural populations of every step, then walk the adjoint back
+    const size_t nbytes = (size_t)Q * c->nSpad * sizeof(float);
+    DBuf<float> nat, adj, adj2;
+    DBuf<uint32_t> nbr;
+    DBuf<double> grads;
+    CK(nat.alloc((size_t)Q * c->nSpad * (size_t)every));
+    CK(adj.alloc((size_t)Q * c->nSpad));
+    CK(adj2.alloc((size_t)Q * c->nSpad));
+    CK(nbr.alloc((size_t)(Q - 1) * c->nSpad));
+    CK(grads.alloc(2));
+    CK(cudaMemsetAsync(adj.p, 0, nbytes, s));
+    CK(cudaMemsetAsync(grads.p, 0, 2 * sizeof(double), s));
+    launch_adj_nbr(make_lat(c), nbr.p, s);
+    CK(cudaGetLastError());
+    const int64_t t_end = c->t;
+    for (int64_t g = nseg - 1; g >= 0; --g) {
+        int64_t n = std::min<int64_t>(every, steps - g * every);
+        int64_t tg = t0 + g * every;
+        CK(cudaMemcpyAsync(c->f.p, ck.p + fbytes * g, fbytes, cudaMemcpyDeviceToDevice, s));
+        unsigned long long tdev = (unsigned long long)tg;
+        CK(cudaMemcpyAsync(&c->st.p->t, &tdev, sizeof(tdev), cudaMemcpyHostToDevice, s));
+        c->t = tg;
+        Lat L = make_lat(c);
+        for (int64_t k = 0; k < n; ++k) {
+            launch_adj_snapshot(L, (c->t & 1) == 1, nat.p + (size_t)Q * c->nSpad * k, s);
+            c->suppress_probe = true;  // the trace is already complete
+            enqueue_step(c, (int)(c->t & 1), false);
+            c->suppress_probe = false;
+            c->t += 1;
+        }
+        CK(cudaGetLastError());
+        AdjArgs A{L, nbr.p, adj.p, c->p.inlet, c->p.outlet, c->p.probe_x};
+        for (int64_t k = n - 1; k >= 0; --k) {
+            int64_t t = tg + k;  // step t -> t + 1
+            A.adj = adj.p;
+            launch_adj_boundary(A, source_shape(c->src, t + 1), grads.p + 1, s);
+            float dlt = (float)(dl[(size_t)(t - t0)] * cs2 / (double)np_plane);
+            launch_adj_step(A, nat.p + (size_t)Q * c->nSpad * k, adj2.p, dlt, grads.p, s);
+            adj.swap(adj2);
+        }
+        CK(cudaGetLastError());
+    }
+    // leave the context where the forward run ended
+    c->t = t_end;
+    {
+        // the last segment's recomputation ended at t_end with the same state
+        unsigned long long tdev = (unsigned long long)t_end;
+        CK(cudaMemcpyAsync(&c->st.p->t, &tdev, sizeof(tdev), cudaMemcpyHostToDevice, s));
+    }
+    double gh[2];
+    CK(cudaMemcpyAsync(gh, grads.p, sizeof(gh), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (loss) *loss = L;
+    const double om = 1.0 / c->p.tau;
+    if (dL_dtau) *dL_dtau = -om * om * gh[0];  // d omega / d tau = -1 / tau^2
+    if (dL_damp) *dL_damp = gh[1];
+    return lbm_dem_status(c);
 }
 
 int lbm_dem_relayout(lbmdem_ctx* c) {

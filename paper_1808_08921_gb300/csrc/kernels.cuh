@@ -137,4 +137,15 @@ void launch_map_update(const Lat& L, const PartView& P, const Band& band, const 
 
 // dem.cu
 void launch_dem_step(const Dem& D, bool init_only, cudaStream_t s);
+// adjoint.cu: reverse-mode kernels of the lattice step for a fixed packing
+struct AdjArgs {
+    Lat L;
+    const uint32_t* nbr;  // [18][nSpad] compact index of x + c_m if fluid, else NONE
+    float* adj;           // [19][nSpad] adjoint of the natural populations
+    int inlet, outlet, probe_x;
+};
+void launch_adj_snapshot(const Lat& L, bool after_even, float* nat, cudaStream_t s);
+void launch_adj_nbr(const Lat& L, uint32_t* nbr, cudaStream_t s);
+void launch_adj_boundary(const AdjArgs& A, double shape, double* d_amp, cudaStream_t s);
+void launch_adj_step(const AdjArgs& A, const float* nat, float* out, float dl, double* d_omega, cudaStream_t s);
 }  // namespace lbmdem

@@ -30,7 +30,8 @@ SYMBOLS = ("lbm_dem_default_params", "lbm_dem_init", "lbm_dem_set_packing",
            "lbm_dem_read_monitors", "lbm_dem_read_counters", "lbm_dem_set_timing",
            "lbm_dem_read_timing", "lbm_dem_last_error", "lbm_dem_destroy",
            "lbm_dem_batch_create", "lbm_dem_batch_step", "lbm_dem_batch_sync",
-           "lbm_dem_batch_graph_launches", "lbm_dem_batch_last_error", "lbm_dem_batch_destroy")
+           "lbm_dem_batch_graph_launches", "lbm_dem_batch_last_error", "lbm_dem_batch_destroy",
+           "lbm_dem_adjoint")
 
 
 class Params(C.Structure):
@@ -92,6 +93,7 @@ def load(build_if_missing: bool = True):
     lib.lbm_dem_last_error.restype = C.c_char_p
     lib.lbm_dem_destroy.argtypes = [vp]
     lib.lbm_dem_destroy.restype = None
+    lib.lbm_dem_adjoint.argtypes = [vp, i64, i32, P(d), P(d), P(d), P(d), P(d)]
     lib.lbm_dem_batch_create.argtypes = [P(vp), i32, P(vp)]
     lib.lbm_dem_batch_step.argtypes = [vp, P(i64)]
     lib.lbm_dem_batch_sync.argtypes = [vp]
@@ -240,6 +242,16 @@ class Sim:
         self._check(load().lbm_dem_read_timing(self._h, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64))))
         names = ("collide_stream", "links", "map_update", "inlet_outlet", "dem")
         return {k: (float(a), int(b)) for k, a, b in zip(names, ms, n)}
+
+    def adjoint(self, steps, every, target):
+        """lbm_dem_adjoint: (loss, dL/dtau, dL/damplitude, pressure trace)."""
+        tgt = np.ascontiguousarray(target, np.float64)
+        assert tgt.shape == (steps,)
+        L, dt, da = C.c_double(), C.c_double(), C.c_double()
+        tr = np.zeros(steps)
+        self._check(load().lbm_dem_adjoint(self._h, int(steps), int(every), _dp(tgt), C.byref(L), C.byref(dt),
+                                           C.byref(da), _dp(tr)))
+        return L.value, dt.value, da.value, tr
 
     def close(self):
         if getattr(self, "_h", None):

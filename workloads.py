@@ -206,3 +206,14 @@ def config_sweep(n: int = 48, seed: int = 4, amplitude: float = 1e-3):
         ws.append(w)
         steps.append(int(math.ceil(L * math.sqrt(3.0))))
     return ws, steps
+
+
+def config_adjoint(steps: int = 5000) -> Workload:
+    """Fixed packing for the adjoint: 64 x 64 x 512 (x = 512), tau 0.6, FCC
+    a = 32 with R = 11.4 (2 x 2 x 16 cells, 256 spheres, every one fixed),
+    sine source amplitude 1e-3 with period 400, probe plane x = 400."""
+    w = fcc_column(512, 64, 64, 0.6, 32.0, 11.4, jitter=1e-3 * 11.4, seed=5, period=400, mu=0.3,
+                   substeps=1, steps=steps, name="fcc64x64x512_a32_R11.4_fixed")
+    w.fixed = np.ones(len(w.R), np.uint8)
+    w.probe_x = 400
+    return w
