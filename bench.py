@@ -139,6 +139,20 @@ def _profiled_traffic(group):
     return val if kh == _kernel_hash() else None
 
 
+def aggregate(ms, fluid, world, device):
+    """Whole-job figures of a multi-rank run (independent columns, one per
+    rank): the slowest rank's time and all ranks' fluid nodes.  The only
+    collective of the benchmark; the step itself exchanges nothing."""
+    if world <= 1:
+        return ms, float(fluid)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, float(fluid)], device=device, dtype=torch.float64)
+    ts = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(ts, t)
+    return max(float(x[0]) for x in ts), sum(float(x[1]) for x in ts)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -183,15 +197,7 @@ def run_ours(args):
     sim.set_timing(False)
     st = sim.status()
     fluid = cnt_b["fluid"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, float(fluid)], device="cuda", dtype=torch.float64)
-        ts = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(ts, t)
-        ms_max = max(float(x[0]) for x in ts)
-        fluid_sum = sum(float(x[1]) for x in ts)
-    else:
-        ms_max, fluid_sum = ms, float(fluid)
+    ms_max, fluid_sum = aggregate(ms, fluid, world, "cuda")
     value = fluid_sum * args.steps / (ms_max * 1e-3) / 1e6
     # rooflines of the HBM-bound kernel groups at their algorithmic bytes
     # (collide+stream: 152 B per fluid node; links: 8 B per link record, the
