@@ -175,6 +175,13 @@ int lbm_dem_read_particles(lbmdem_ctx* c, double* X, double* V, double* Omega, d
 int lbm_dem_read_particles_noalloc(lbmdem_ctx* c, double* X, double* V, double* Omega,
                                    double* quat, double* F_hyd, double* T_hyd);
 
+/* Plane averages of the current state over the fluid nodes of every x plane
+ * (the space-time data whose discrete Fourier transform gives the dispersion
+ * relation, Section 3.2): rho[nx] = mean density, jx[nx] = mean
+ * rho u_x (Eq. 7); NaN for a plane without fluid; either pointer may be NULL.
+ * Synchronises. */
+int lbm_dem_read_plane_means(lbmdem_ctx* c, double* rho, double* jx);
+
 /* Probe trace: trace[k] = mean density over the fluid nodes of plane probe_x
  * entering step k (after that step's map update), k = 0 .. len-1.  Copies
  * min(len, max_len) values; *len receives the full length.  Synchronises. */

@@ -1437,6 +1437,28 @@ int lbm_dem_read_fields(lbmdem_ctx* c, double* rho, double* u, uint8_t* solid) {
     return lbm_dem_status(c);
 }
 
+int lbm_dem_read_plane_means(lbmdem_ctx* c, double* rho, double* jx) {
+    if (!c) return LBMDEM_ERR_INVALID_ARG;
+    if (!c->have_packing) return fail(c, LBMDEM_ERR_STATE, "no packing");
+    if (!c->lbm) return fail(c, LBMDEM_ERR_STATE, "fluid is off");
+    CK(cudaSetDevice(c->p.device));
+    const int nx = c->p.nx;
+    DBuf<double> d;
+    CK(d.alloc(3 * (size_t)nx));
+    CK(cudaMemsetAsync(d.p, 0, sizeof(double) * 3 * nx, c->stream));
+    launch_plane_sums(make_lat(c), (c->t & 1) == 1, d.p, c->stream);
+    CK(cudaGetLastError());
+    std::vector<double> h(3 * (size_t)nx);
+    CK(cudaMemcpyAsync(h.data(), d.p, sizeof(double) * 3 * nx, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int x = 0; x < nx; ++x) {
+        double n = h[3 * x + 2];
+        if (rho) rho[x] = n > 0 ? c->p.rho_f + h[3 * x] / n : nan("");
+        if (jx) jx[x] = n > 0 ? h[3 * x + 1] / n : nan("");
+    }
+    return lbm_dem_status(c);
+}
+
 __global__ void k_probe_out(const double* sums, int64_t n, double rho_f, double* out) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;

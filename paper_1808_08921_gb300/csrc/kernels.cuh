@@ -127,6 +127,7 @@ struct Dem {
 // lattice.cu
 void launch_collide(const Lat& L, const Mon& mon, bool odd, bool monitor, int tile, cudaStream_t s);
 void launch_inlet_outlet(const Lat& L, const BC& bc, bool after_even, cudaStream_t s);
+void launch_plane_sums(const Lat& L, bool after_even, double* out, cudaStream_t s);
 void launch_read_fields(const Lat& L, bool after_even, double* rho, double* u, uint8_t* solid,
                         cudaStream_t s);
 

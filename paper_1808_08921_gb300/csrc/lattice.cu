@@ -489,4 +489,56 @@ void launch_read_fields(const Lat& L, bool after_even, double* rho, double* u, u
     else k_read_fields<2><<<blocks, 256, 0, s>>>(L, after_even, rho, u, solid);
 }
 
+// ------------------------------------------------------------ plane means
+
+// Sums over the fluid nodes of every x plane of the current state: out[3 x]
+// += sum (rho - rho_f), out[3 x + 1] += sum rho u_x, out[3 x + 2] += count.
+// Consecutive compact nodes share a plane, so each warp reduces runs of
+// equal x before one FP64 atomic per run head.
+template <int ST>
+__global__ void k_plane_sums(Lat L, bool after_even, double* out) {
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    float d = 0.f, jx = 0.f, n = 0.f;
+    int x = -1;
+    if (i < L.nS && fluid_bit(L, i)) {
+        int y, z;
+        unpack_coord(L.coord[i], x, y, z);
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            float g = to_f<ST>(*pop_loc<ST>(L, after_even, x, y, z, i, m), L.fsi);
+            d += g;
+            jx += cx(m) * g;
+        }
+        n = 1.f;
+    }
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    // sums over the lanes of the warp that share this lane's plane; the
+    // lowest such lane adds them (compact order keeps most warps in one plane)
+    double sd = 0.0, sj = 0.0, sn = 0.0;
+    for (int l = 0; l < 32; ++l) {
+        float a = __shfl_sync(full, d, l), b = __shfl_sync(full, jx, l), c = __shfl_sync(full, n, l);
+        int xl = __shfl_sync(full, x, l);
+        if (xl == x) {
+            sd += a;
+            sj += b;
+            sn += c;
+        }
+    }
+    unsigned peers = __match_any_sync(full, x);
+    if (x >= 0 && lane == __ffs(peers) - 1) {
+        atomicAdd(&out[3 * x], sd);
+        atomicAdd(&out[3 * x + 1], sj);
+        atomicAdd(&out[3 * x + 2], sn);
+    }
+}
+
+void launch_plane_sums(const Lat& L, bool after_even, double* out, cudaStream_t s) {
+    unsigned blocks = (L.nS + 255) / 256;
+    if (!blocks) return;
+    if (L.st == 0) k_plane_sums<0><<<blocks, 256, 0, s>>>(L, after_even, out);
+    else if (L.st == 1) k_plane_sums<1><<<blocks, 256, 0, s>>>(L, after_even, out);
+    else k_plane_sums<2><<<blocks, 256, 0, s>>>(L, after_even, out);
+}
+
 }  // namespace lbmdem

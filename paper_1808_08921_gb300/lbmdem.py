@@ -31,7 +31,7 @@ SYMBOLS = ("lbm_dem_default_params", "lbm_dem_init", "lbm_dem_set_packing",
            "lbm_dem_read_timing", "lbm_dem_last_error", "lbm_dem_destroy",
            "lbm_dem_batch_create", "lbm_dem_batch_step", "lbm_dem_batch_sync",
            "lbm_dem_batch_graph_launches", "lbm_dem_batch_last_error", "lbm_dem_batch_destroy",
-           "lbm_dem_adjoint")
+           "lbm_dem_adjoint", "lbm_dem_read_plane_means")
 
 
 class Params(C.Structure):
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
     lib.lbm_dem_destroy.argtypes = [vp]
     lib.lbm_dem_destroy.restype = None
     lib.lbm_dem_adjoint.argtypes = [vp, i64, i32, P(d), P(d), P(d), P(d), P(d)]
+    lib.lbm_dem_read_plane_means.argtypes = [vp, P(d), P(d)]
     lib.lbm_dem_batch_create.argtypes = [P(vp), i32, P(vp)]
     lib.lbm_dem_batch_step.argtypes = [vp, P(i64)]
     lib.lbm_dem_batch_sync.argtypes = [vp]
@@ -242,6 +243,12 @@ class Sim:
         self._check(load().lbm_dem_read_timing(self._h, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64))))
         names = ("collide_stream", "links", "map_update", "inlet_outlet", "dem")
         return {k: (float(a), int(b)) for k, a, b in zip(names, ms, n)}
+
+    def plane_means(self):
+        """(rho[nx], rho u_x[nx]): averages over the fluid nodes of each x plane."""
+        rho, jx = np.zeros(self.shape[0]), np.zeros(self.shape[0])
+        self._check(load().lbm_dem_read_plane_means(self._h, _dp(rho), _dp(jx)))
+        return rho, jx
 
     def adjoint(self, steps, every, target):
         """lbm_dem_adjoint: (loss, dL/dtau, dL/damplitude, pressure trace)."""
