@@ -97,7 +97,7 @@ typedef struct {
     int32_t monitor_every;/* accumulate FP64 mass/momentum every M steps; 0 = off     */
     int32_t graph_steps;  /* steps per captured CUDA graph (even); 0 picks 16         */
     int32_t max_flips;    /* node conversions per step the scratch holds; 0 = auto    */
-    int32_t tile;         /* threads per block of collide+stream: 64, 128 or 256 (0)  */
+    int32_t tile;         /* threads per block of collide+stream: 64, 128 (0) or 256  */
     int32_t device;       /* CUDA device ordinal                                      */
     void* cuda_stream;    /* cudaStream_t to issue on; NULL = a stream of the context */
 } lbmdem_params;

@@ -571,7 +571,7 @@ static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
             cudaMemsetAsync(&sd->max_u_bits, 0, sizeof(uint32_t), s);
         }
         if (tm) record_pair_begin(c, 0, e);
-        launch_collide(L, mon, parity == 1, monitor, c->p.tile > 0 ? c->p.tile : 256, s);
+        launch_collide(L, mon, parity == 1, monitor, c->p.tile > 0 ? c->p.tile : 128, s);
         if (tm) record_pair_end(c, e);
         LinkLists LL{c->surf_link.p, c->warp_p.p, c->chunk_dir.p, c->nwarps};
         if (tm) record_pair_begin(c, 1, e);

@@ -28,13 +28,13 @@
 
 namespace lbmdem {
 
-__device__ __forceinline__ int imin_wrap(int d, int L) {
-    // minimum image of an integer offset (any magnitude)
-    d %= L;
-    if (d < 0) d += L;
-    if (d > L / 2) d -= L;
+// minimum image of an offset -L < d < L
+__device__ __forceinline__ int imin_small(int d, int L) {
+    if (2 * d > L) return d - L;
+    if (2 * d < -L) return d + L;
     return d;
 }
+
 
 // Direction m at run time (warp-uniform in the link kernel), from bit masks of
 // the velocity set of Eq. 3: one compact body instead of 18 specialisations
@@ -263,6 +263,8 @@ __global__ void k_map_band(MapArgs A) {
     const Lat& L = A.L;
     int x, y, z;
     unpack_coord(A.band.coord[k], x, y, z);
+    const size_t li = ((size_t)x * L.ny + y) * L.nz + z;
+    const int old = L.owner[li];  // issued early: independent of the test
     int4 cand = A.band.cand[k];
     int c4[4] = {cand.x, cand.y, cand.z, cand.w};
     int best = OWNER_FLUID;
@@ -275,10 +277,10 @@ __global__ void k_map_band(MapArgs A) {
         for (int a = 0; a < 4; ++a) {
             int p = c4[a];
             if (p < 0) break;
-            int4 o = A.P.org[p];
+            int4 o = A.P.orgw[p];  // origin wrapped into the box: |node - o| < L
             float4 xf = A.P.xf[p];
-            int ix = L.px ? imin_wrap(x - o.x, L.nx) : x - o.x;
-            int iy = imin_wrap(y - o.y, L.ny), iz = imin_wrap(z - o.z, L.nz);
+            int ix = L.px ? imin_small(x - o.x, L.nx) : x - o.x;
+            int iy = imin_small(y - o.y, L.ny), iz = imin_small(z - o.z, L.nz);
             float ax = __fsub_rn((float)ix, xf.x), ay = __fsub_rn((float)iy, xf.y), az = __fsub_rn((float)iz, xf.z);
             float d2 = norm2_rn(ax, ay, az);
             float R2 = __fmul_rn(A.P.R[p], A.P.R[p]);
@@ -320,8 +322,6 @@ __global__ void k_map_band(MapArgs A) {
             }
         }
     }
-    size_t li = ((size_t)x * L.ny + y) * L.nz + z;
-    int old = L.owner[li];
     if (old != best) {
         uint32_t slot = atomicAdd(&A.st->nflip[A.par], 1u);
         if (slot < A.F.cap) {
