@@ -72,3 +72,29 @@ def test_storage_error_against_oracle(reference, storage):
         assert same, "solid maps differ"
         assert drho <= br and du <= bu and dx <= bx, (drho, du, dx)
     g.close()
+
+
+@pytest.mark.parametrize("storage", [lbmdem.F16_DEV, lbmdem.BF16_DEV])
+def test_16bit_storage_through_conversions_and_relayout(storage):
+    """Spheres moving ~1 lu in a periodic box (nodes covered and uncovered,
+    16-bit gather/scatter of the conversions) and a forced re-layout (the
+    stored 16-bit populations move without conversion)."""
+    w = workloads.random_small(1, nx=22, ny=14, nz=12, n=3, R=3.1, tau=0.8, mobile=True, vel=0.05)
+    w.inlet = workloads.X_PERIODIC
+    w.rho_p, w.dem_substeps = 3.0, 3
+    g = lbmdem.Sim.from_workload(w, skin=0.6, dem_skin=1.2, storage=storage)
+    o = oracle.Oracle(w)
+    g.step(20)
+    o.step(20)
+    r0, u0, s0 = g.fields()
+    g.relayout()
+    r1, u1, s1 = g.fields()
+    assert np.array_equal(s0, s1) and np.array_equal(r0, r1) and np.array_equal(u0, u1)
+    g.step(21)
+    o.step(21)
+    assert g.counters()["conversions"] > 30
+    same, drho, du, dx = _errors(g, o)
+    print(f"storage {storage} moving: |drho|/rho' {drho:.2e}  |du|/umax {du:.2e}  |dX| {dx:.2e} lu")
+    assert same
+    br, bu, bx = BARS[storage]
+    assert drho <= 10 * br and du <= bu and dx <= 10 * bx
