@@ -71,6 +71,8 @@ struct lbmdem_ctx {
     int status_latched = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t side = nullptr;             // inlet/outlet, beside the DEM
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int nw = 0;
     size_t N = 0, W = 0;
     bool lbm = true;
@@ -267,7 +269,6 @@ static Dem make_dem(lbmdem_ctx* c) {
     D.status = &s->status;
     D.max_disp_bits = &s->max_disp_bits;
     D.max_vel_bits = &s->max_vel_bits;
-    D.t_dev = &s->t;
     D.hard_disp = (float)c->hard;
     D.px = c->p.inlet == LBMDEM_X_PERIODIC;
     D.Lx = c->p.nx;
@@ -506,7 +507,8 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
 
 // ------------------------------------------------------------ stepping
 
-static void record_pair_begin(lbmdem_ctx* c, int group, size_t& idx) {
+static void record_pair_begin(lbmdem_ctx* c, int group, size_t& idx, cudaStream_t st = nullptr) {
+    if (!st) st = c->stream;
     idx = c->ev_pairs++;
     while (c->ev.size() < 2 * c->ev_pairs) {
         cudaEvent_t e;
@@ -516,16 +518,17 @@ static void record_pair_begin(lbmdem_ctx* c, int group, size_t& idx) {
     if (c->ev_group.size() < c->ev_pairs) c->ev_group.resize(c->ev_pairs);
     c->ev_group[idx] = group;
     if (c->capturing)
-        cudaEventRecordWithFlags(c->ev[2 * idx], c->stream, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(c->ev[2 * idx], st, cudaEventRecordExternal);
     else
-        cudaEventRecord(c->ev[2 * idx], c->stream);
+        cudaEventRecord(c->ev[2 * idx], st);
 }
 
-static void record_pair_end(lbmdem_ctx* c, size_t idx) {
+static void record_pair_end(lbmdem_ctx* c, size_t idx, cudaStream_t st = nullptr) {
+    if (!st) st = c->stream;
     if (c->capturing)
-        cudaEventRecordWithFlags(c->ev[2 * idx + 1], c->stream, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(c->ev[2 * idx + 1], st, cudaEventRecordExternal);
     else
-        cudaEventRecord(c->ev[2 * idx + 1], c->stream);
+        cudaEventRecord(c->ev[2 * idx + 1], st);
 }
 
 // kernels one step issues: map update (4 when there is a band, else 1),
@@ -540,6 +543,10 @@ static int64_t kernels_per_step(const lbmdem_ctx* c) {
         k += (!px && !(c->p.inlet != 0 && c->p.outlet > 1)) ? 1 : 0;
     }
     return k;
+}
+
+static bool inlet_outlet_active(const lbmdem_ctx* c) {
+    return c->p.inlet != LBMDEM_X_PERIODIC && !(c->p.inlet != 0 && c->p.outlet > 1);
 }
 
 static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
@@ -577,10 +584,25 @@ static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
         if (tm) record_pair_begin(c, 1, e);
         launch_links(L, P, LL, s);
         if (tm) record_pair_end(c, e);
+        // the inlet/outlet only needs this step's populations and the DEM only
+        // this step's link sums: they run side by side, the boundary on a
+        // side stream joined before the next step
         BC bc{c->p.inlet, c->p.outlet, c->src, &sd->t};
-        if (tm) record_pair_begin(c, 3, e);
-        launch_inlet_outlet(L, bc, parity == 0, s);
-        if (tm) record_pair_end(c, e);
+        if (inlet_outlet_active(c)) {
+            cudaEventRecord(c->ev_fork, s);
+            cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+            size_t e2 = 0;
+            if (tm) record_pair_begin(c, 3, e2, c->side);
+            launch_inlet_outlet(L, bc, parity == 0, c->side);
+            if (tm) record_pair_end(c, e2, c->side);
+            cudaEventRecord(c->ev_join, c->side);
+            Dem D = make_dem(c);
+            if (tm) record_pair_begin(c, 4, e);
+            launch_dem_step(D, false, s);
+            if (tm) record_pair_end(c, e);
+            cudaStreamWaitEvent(s, c->ev_join, 0);
+            return;
+        }
     }
     Dem D = make_dem(c);
     if (tm) record_pair_begin(c, 4, e);
@@ -771,6 +793,10 @@ int lbm_dem_init(const lbmdem_params* pp, lbmdem_ctx** out) {
             return bail(LBMDEM_ERR_CUDA);
         c->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return bail(LBMDEM_ERR_CUDA);
     if (c->st.alloc(1) != cudaSuccess) return bail(LBMDEM_ERR_OOM);
     if (cudaMallocHost((void**)&c->st_host, sizeof(DevStats)) != cudaSuccess) return bail(LBMDEM_ERR_OOM);
     if (cudaMemset(c->st.p, 0, sizeof(DevStats)) != cudaSuccess) return bail(LBMDEM_ERR_CUDA);
@@ -1565,6 +1591,10 @@ void lbm_dem_destroy(lbmdem_ctx* c) {
     destroy_graph(c);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->st_host) cudaFreeHost(c->st_host);
+    if (c->side) cudaStreamSynchronize(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaSetDevice(c->p.device);
     delete c;  // device buffers are released by their destructors

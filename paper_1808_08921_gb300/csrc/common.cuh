@@ -252,7 +252,8 @@ struct DevStats {
     uint32_t max_disp_bits;  // float bits of max |dX| (non-negative)
     uint32_t max_vel_bits;   // float bits of max |V|
     uint32_t pad0;
-    unsigned long long t;    // completed steps
+    unsigned long long t;    // steps begun (the map update counts each step first; between
+                             // steps it equals the completed steps)
     unsigned long long flips_total;
     double mon[6];           // sum rho, sum rho u, max|u|, step
     uint32_t max_u_bits;

@@ -251,7 +251,10 @@ struct MapArgs {
 
 __global__ void k_map_band(MapArgs A) {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0) A.st->nflip[A.par ^ 1] = 0;
+    if (k == 0) {
+        A.st->nflip[A.par ^ 1] = 0;
+        A.st->t += 1ull;  // the step starts: t counts it from here on
+    }
     if (k < (uint32_t)A.P.n) {
         for (int r = 0; r < NREP; ++r)
             for (int a = 0; a < 3; ++a) {

@@ -315,7 +315,6 @@ __global__ void k_dem_step(Dem D, int init_only) {
     }
     flush_maxima(D, dmax, vmax, bad);
     cl.sync();
-    if (tid == 0 && !init_only) *D.t_dev += 1ull;
 }
 
 // The same K substeps with every sphere's state in registers of its team and
@@ -459,7 +458,6 @@ __global__ void __launch_bounds__(DSM_THREADS, 1) k_dem_step_dsm(Dem D) {
     uint32_t bad = 0;
     if (have && tl == 0) sphere_frame(D, i, dmax, vmax, bad);
     flush_maxima(D, dmax, vmax, bad);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *D.t_dev += 1ull;
 }
 
 // Largest cluster (CTAs of DSM_THREADS threads) the DSM kernel can run with

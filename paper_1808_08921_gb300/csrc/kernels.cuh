@@ -118,7 +118,6 @@ struct Dem {
     uint32_t* status;
     uint32_t* max_disp_bits;
     uint32_t* max_vel_bits;
-    unsigned long long* t_dev;   // incremented at the end of the step
     float hard_disp;             // displacement at which the layout is invalid
     int px;
     double Lx, Ly, Lz;

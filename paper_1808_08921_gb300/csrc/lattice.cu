@@ -109,7 +109,7 @@ __device__ __forceinline__ void mon_flush(const MonAcc& a, const Mon& mon, bool 
                 c += __shfl_xor_sync(full, c, o);
             }
             if ((threadIdx.x & 31) == 0) {
-                unsigned long long t = *mon.t_dev;
+                unsigned long long t = *mon.t_dev - 1ull;  // the map update counted this step
                 atomicAdd(&mon.probe_sum[2 * t], (double)s);
                 atomicAdd(&mon.probe_sum[2 * t + 1], (double)c);
             }
@@ -386,7 +386,8 @@ template <bool AFTER_EVEN, int ST>
 __global__ void k_inlet_outlet(Lat L, BC bc) {
     auto* f = pops<ST>(L);
     __shared__ float s_drho;
-    if (threadIdx.x == 0) s_drho = (float)source_drho(bc.src, *bc.t_dev + 1ull);
+    // the density the step ends with: t + 1, counted by the map update
+    if (threadIdx.x == 0) s_drho = (float)source_drho(bc.src, *bc.t_dev);
     __syncthreads();
     int plane = L.ny * L.nz;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
