@@ -110,6 +110,7 @@ struct lbmdem_ctx {
     DBuf<double> Xref, Fh, Th, Rd, Fh_prev, Th_prev;
     DBuf<float4> Fa, Ta;
     DBuf<float4> dX, dXc, dXb, V, Om, q, Vhb, Whb, Fc, Tc, xf;
+    DBuf<float4> ab;  // [n][Q-1] per-step link terms, written by the map update
     DBuf<int4> org, orgw;
     DBuf<float> R, invm, invI;
     DBuf<uint8_t> fixed;
@@ -221,6 +222,7 @@ static PartView make_part(lbmdem_ctx* c) {
     P.org = c->org.p;
     P.orgw = c->orgw.p;
     P.xf = c->xf.p;
+    P.ab = c->ab.p;
     P.Fh = c->Fh.p;
     P.Th = c->Th.p;
     return P;
@@ -887,6 +889,7 @@ int lbm_dem_set_packing(lbmdem_ctx* c, int32_t n, const double* X, const double*
     CK(c->Fc.alloc(nn));
     CK(c->Tc.alloc(nn));
     CK(c->xf.alloc(nn));
+    CK(c->ab.alloc((Q - 1) * nn));
     CK(c->org.alloc(nn));
     CK(c->orgw.alloc(nn));
     CK(c->R.alloc(nn));

@@ -202,6 +202,7 @@ struct PartView {
     const int4* org;      // [n] integer origin floor(Xref)
     const int4* orgw;     // [n] that origin wrapped into the box (periodic axes)
     const float4* xf;     // [n] X(t) - origin, FP32
+    float4* ab;           // [n][Q-1] moving-wall terms of the step's links (alpha - xf.beta, beta)
     double* Fh;           // [NREP][n][3] hydrodynamic force accumulators (summed by the DEM)
     double* Th;           // [NREP][n][3] hydrodynamic torque accumulators
 };

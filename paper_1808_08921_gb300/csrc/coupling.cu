@@ -36,47 +36,7 @@ __device__ __forceinline__ int imin_small(int d, int L) {
 }
 
 
-// Direction m at run time (warp-uniform in the link kernel), from bit masks of
-// the velocity set of Eq. 3: one compact body instead of 18 specialisations
-// keeps the kernel inside the instruction cache.
-constexpr uint32_t DPX = (1u << 0) | (1u << 6) | (1u << 7) | (1u << 8) | (1u << 9);
-constexpr uint32_t DNX = (1u << 1) | (1u << 10) | (1u << 11) | (1u << 12) | (1u << 13);
-constexpr uint32_t DPY = (1u << 2) | (1u << 6) | (1u << 10) | (1u << 14) | (1u << 15);
-constexpr uint32_t DNY = (1u << 3) | (1u << 7) | (1u << 11) | (1u << 16) | (1u << 17);
-constexpr uint32_t DPZ = (1u << 4) | (1u << 8) | (1u << 12) | (1u << 14) | (1u << 16);
-constexpr uint32_t DNZ = (1u << 5) | (1u << 9) | (1u << 13) | (1u << 15) | (1u << 17);
-// opposites, 5 bits each: m 0..11 in the low word, 12..18 in the high word
-constexpr unsigned long long DOLO = 1ull | (0ull << 5) | (3ull << 10) | (2ull << 15) | (5ull << 20) |
-                                    (4ull << 25) | (11ull << 30) | (10ull << 35) | (13ull << 40) |
-                                    (12ull << 45) | (7ull << 50) | (6ull << 55);
-constexpr unsigned long long DOHI = 9ull | (8ull << 5) | (17ull << 10) | (16ull << 15) | (15ull << 20) |
-                                    (14ull << 25) | (18ull << 30);
-__host__ __device__ constexpr int rcx(int m) { return (int)((DPX >> m) & 1u) - (int)((DNX >> m) & 1u); }
-__host__ __device__ constexpr int rcy(int m) { return (int)((DPY >> m) & 1u) - (int)((DNY >> m) & 1u); }
-__host__ __device__ constexpr int rcz(int m) { return (int)((DPZ >> m) & 1u) - (int)((DNZ >> m) & 1u); }
-__host__ __device__ constexpr int ropp(int m) {
-    return m < 12 ? (int)((DOLO >> (5 * m)) & 31ull) : (int)((DOHI >> (5 * (m - 12))) & 31ull);
-}
-constexpr bool dir_tables_agree(int m) {
-    return m == Q ? true
-                  : (rcx(m) == cx(m) && rcy(m) == cy(m) && rcz(m) == cz(m) && ropp(m) == opp(m) &&
-                     dir_tables_agree(m + 1));
-}
-static_assert(dir_tables_agree(0), "run-time direction decoding disagrees with Eq. 3 tables");
-
-struct Dir {
-    int cx, cy, cz, op;
-    float w;
-    __device__ __forceinline__ explicit Dir(int m) {
-        cx = rcx(m);
-        cy = rcy(m);
-        cz = rcz(m);
-        op = ropp(m);
-        w = (cx * cx + cy * cy + cz * cz) == 1 ? 1.0f / 18.0f : 1.0f / 36.0f;
-    }
-};
-
-// The same directions as a constant table, read with a warp-uniform index.
+// Directions of Eq. 3 as a constant table, read with a warp-uniform index.
 struct DirC {
     float cx, cy, cz, w;
     int op;
@@ -101,38 +61,39 @@ __device__ __forceinline__ float rel_f(uint32_t word, int shift) {
     return __uint_as_float(0x4B000000u | ((word >> shift) & 255u)) - 8388736.0f;
 }
 
-// Does sphere p own the band neighbour x + c_m of the link node now?
-// Decided by the map update's FP32 test (same operands and rounding) away
-// from its margin, else (or when several spheres may claim the node) by
-// the owner map.
-__device__ __forceinline__ bool owns_neighbour(const Lat& L, const PartView& P, int p, uint32_t y, int m,
+// Does sphere p own the band neighbour x + c of the link node now (c the
+// link's direction)?  Decided by the map update's FP32 test (same operands
+// and rounding) away from its margin, else (or when several spheres may
+// claim the node) by the owner map.
+__device__ __forceinline__ bool owns_neighbour(const Lat& L, const PartView& P, int p, uint32_t y, const DirC& d,
                                                const float4& xf, float R2) {
-    const Dir d(m);
     if (!(y >> 25 & 1u)) {
-        float ax = __fsub_rn(rel_f(y, 0) + (float)d.cx, xf.x), ay = __fsub_rn(rel_f(y, 8) + (float)d.cy, xf.y),
-              az = __fsub_rn(rel_f(y, 16) + (float)d.cz, xf.z);
+        float ax = __fsub_rn(rel_f(y, 0) + d.cx, xf.x), ay = __fsub_rn(rel_f(y, 8) + d.cy, xf.y),
+              az = __fsub_rn(rel_f(y, 16) + d.cz, xf.z);
         float d2 = norm2_rn(ax, ay, az);
         if (fabsf(d2 - R2) > FP32_MARGIN * R2) return d2 < R2;
     }
     int ix = (int)(y & 255u) - 128, iy = (int)((y >> 8) & 255u) - 128, iz = (int)((y >> 16) & 255u) - 128;
     int4 o = P.orgw[p];  // wrapped origin: the offsets are small
-    int xs = o.x + ix + d.cx, ys = o.y + iy + d.cy, zs = o.z + iz + d.cz;
+    int xs = o.x + ix + (int)d.cx, ys = o.y + iy + (int)d.cy, zs = o.z + iz + (int)d.cz;
     if (L.px) xs = xs < 0 ? xs + L.nx : (xs >= L.nx ? xs - L.nx : xs);
     ys = ys < 0 ? ys + L.ny : (ys >= L.ny ? ys - L.ny : ys);
     zs = zs < 0 ? zs + L.nz : (zs >= L.nz ? zs - L.nz : zs);
     return L.owner[((size_t)xs * L.ny + ys) * L.nz + zs] == p;
 }
 
-// One warp: LINK_WARP links of one sphere in four chunks of 32, each chunk in
-// one direction.  The phases (records, fluid bits, ownership, populations,
-// updates) each issue all of the thread's loads before using any.  With c
-// uniform over a chunk, the moving-wall term of Eq. 14 is
-// 6 w rho_f c.(V + W x b) = alpha + r.beta with alpha = 6 w rho_f c.V and
-// beta = 6 w rho_f (c x W) (b = r + c/2 and c.(W x c) = 0).  Warp-shuffle
-// sums, then one FP64 atomic per component per warp into one of NREP
-// accumulator copies of the sphere.
+// One warp: LINK_WARP links of one sphere in chunks of 32, each chunk in one
+// direction.  The phases (records, fluid bits, ownership, populations,
+// updates) each issue all of the thread's loads before using any.  The
+// moving-wall term of Eq. 14 at the link node x = origin + rel is
+// 6 w rho_f c.(V + W x (b - X)) = alpha' + rel.beta, b = x + c/2 (c.(W x c)
+// = 0), with alpha' and beta per (sphere, direction) from the map update.
+// The torque (Eq. 19) is summed about the sphere's lattice origin and moved
+// to the centre once per warp: sum r x (c q) = sum rel x (c q) - xf x F.
+// Warp-shuffle sums, then one FP64 atomic per component per warp into one
+// of NREP accumulator copies of the sphere.
 template <int ST>
-__global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
+__global__ void __launch_bounds__(256, 4) k_links(Lat L, PartView P, LinkLists B) {
     constexpr int K = LINK_CHUNKS;
     auto* f = pops<ST>(L);
     // warps in reverse order: the last spheres' nodes were collided last and
@@ -148,7 +109,7 @@ __global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
 #pragma unroll
     for (int k = 0; k < K; ++k) lk[k] = __ldcs(&rec[k * 32]);
     const float4 xf = P.xf[p];
-    const float4 V = P.V[p], W = P.W[p];
+    const float4* ab = P.ab + (size_t)p * (Q - 1);
     bool on[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) on[k] = lk[k].x != NONE;
@@ -157,12 +118,12 @@ __global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
 #pragma unroll
         for (int k = 0; k < K; ++k)  // only a node inside a band can have been covered
             fb[k] = on[k] && (lk[k].y >> 26 & 1u) ? __ldg(&L.fbits[lk[k].x >> 5]) : ~0u;
+        const float R2 = __fmul_rn(P.R[p], P.R[p]);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             on[k] = on[k] && ((fb[k] >> (lk[k].x & 31)) & 1u);
             if (on[k] && (lk[k].y >> 24 & 1u))
-                on[k] = owns_neighbour(L, P, p, lk[k].y, (int)((dirs >> (8 * k)) & 31u), xf,
-                                       __fmul_rn(P.R[p], P.R[p]));
+                on[k] = owns_neighbour(L, P, p, lk[k].y, kDir[(dirs >> (8 * k)) & 31u], xf, R2);
         }
     }
     float v[K];
@@ -172,25 +133,22 @@ __global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
         v[k] = on[k] ? to_f<ST>(f[(size_t)op * L.nSpad + lk[k].x], L.fsi) : 0.f;
     }
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const float s6 = 6.0f * L.rho_f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const DirC d = kDir[(dirs >> (8 * k)) & 31u];
-        const float sw = s6 * d.w;
-        const float alpha = sw * (d.cx * V.x + d.cy * V.y + d.cz * V.z);
-        const float bx = sw * (d.cy * W.z - d.cz * W.y), by = sw * (d.cz * W.x - d.cx * W.z),
-                    bz = sw * (d.cx * W.y - d.cy * W.x);
+        const uint32_t m = (dirs >> (8 * k)) & 31u;
+        const DirC d = kDir[m];
+        const float4 a = ab[m];
         if (!on[k]) continue;
         const uint32_t y = lk[k].y;
-        const float rx = rel_f(y, 0) - xf.x, ry = rel_f(y, 8) - xf.y, rz = rel_f(y, 16) - xf.z;
-        const float delta = alpha + (rx * bx + ry * by + rz * bz);
+        const float rx = rel_f(y, 0), ry = rel_f(y, 8), rz = rel_f(y, 16);
+        const float delta = a.x + (rx * a.y + ry * a.z + rz * a.w);
         f[(size_t)d.op * L.nSpad + lk[k].x] = from_f<ST>(v[k] - delta, L.fs);
         const float q = 2.0f * v[k] - delta;
         const float qx = d.cx * q, qy = d.cy * q, qz = d.cz * q;
         acc[0] += qx;
         acc[1] += qy;
         acc[2] += qz;
-        // b x (c q) = r x (c q) since c x c = 0
+        // b x (c q) = r x (c q) since c x c = 0; r = rel - xf
         acc[3] += ry * qz - rz * qy;
         acc[4] += rz * qx - rx * qz;
         acc[5] += rx * qy - ry * qx;
@@ -201,6 +159,9 @@ __global__ void __launch_bounds__(256) k_links(Lat L, PartView P, LinkLists B) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) acc[c] += __shfl_xor_sync(full, acc[c], o);
     if (lane == 0) {
+        acc[3] -= xf.y * acc[2] - xf.z * acc[1];
+        acc[4] -= xf.z * acc[0] - xf.x * acc[2];
+        acc[5] -= xf.x * acc[1] - xf.y * acc[0];
         size_t rep = (size_t)(w % NREP) * P.n + p;
         double* F = P.Fh + 3 * rep;
         double* T = P.Th + 3 * rep;
@@ -261,6 +222,21 @@ __global__ void k_map_band(MapArgs A) {
                 A.P.Fh[3 * ((size_t)r * A.P.n + k) + a] = 0.0;
                 A.P.Th[3 * ((size_t)r * A.P.n + k) + a] = 0.0;
             }
+        // moving-wall terms of this step's links of sphere k, per direction
+        // m: beta = 6 w rho_f (c x W) and alpha' = 6 w rho_f c.V - xf.beta,
+        // so that the term of Eq. 14 at a link node with offset rel from the
+        // sphere's lattice origin is alpha' + rel.beta
+        const float4 V = A.P.V[k], W = A.P.W[k], xf = A.P.xf[k];
+        const float s6 = 6.0f * A.L.rho_f;
+#pragma unroll
+        for (int m = 0; m < Q - 1; ++m) {
+            const float sw = s6 * wt(m);
+            const float ex = (float)cx(m), ey = (float)cy(m), ez = (float)cz(m);
+            const float bx = sw * (ey * W.z - ez * W.y), by = sw * (ez * W.x - ex * W.z),
+                        bz = sw * (ex * W.y - ey * W.x);
+            const float alpha = sw * (ex * V.x + ey * V.y + ez * V.z);
+            A.P.ab[(size_t)k * (Q - 1) + m] = make_float4(alpha - (xf.x * bx + xf.y * by + xf.z * bz), bx, by, bz);
+        }
     }
     if (k >= A.band.n) return;
     const Lat& L = A.L;
