@@ -66,7 +66,8 @@ __device__ __forceinline__ void pair_contact(const Dem& D, float Ri, float Rj, f
     }
     float dist = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
     float delta = qd / (cut + dist);
-    float3 n = make_float3(d.x / dist, d.y / dist, d.z / dist);
+    float idist = 1.0f / dist;  // |d| is the same for both spheres: n stays mirror-exact
+    float3 n = make_float3(d.x * idist, d.y * idist, d.z * idist);
     float Rs = Ri * Rj / (Ri + Rj);
     float sq = sqrtf(Rs * delta);
     float fn = D.kn * sq * delta;
@@ -81,10 +82,10 @@ __device__ __forceinline__ void pair_contact(const Dem& D, float Ri, float Rj, f
     float hn = h.x * n.x + h.y * n.y + h.z * n.z;
     float kdt = D.kt * sq * dt_inc;
     float3 ft = make_float3(h.x - hn * n.x + kdt * vt.x, h.y - hn * n.y + kdt * vt.y, h.z - hn * n.z + kdt * vt.z);
-    float ftm = sqrtf(ft.x * ft.x + ft.y * ft.y + ft.z * ft.z);
+    float ftm2 = ft.x * ft.x + ft.y * ft.y + ft.z * ft.z;
     float cap = D.mu * fn;
-    if (ftm > cap) {
-        float sc = cap / ftm;
+    if (ftm2 > cap * cap) {  // |F_t| > mu |F_n|, compared in squares
+        float sc = cap / sqrtf(ftm2);
         ft = make_float3(ft.x * sc, ft.y * sc, ft.z * sc);
     }
     h = make_float4(ft.x, ft.y, ft.z, 0.f);
@@ -191,6 +192,29 @@ __device__ __forceinline__ void sphere_frame(const Dem& D, int i, float& dmax, f
     else if (dd >= D.hard_disp) bad |= ST_SKIN;
     dmax = fmaxf(dmax, dd);
     vmax = fmaxf(vmax, vv);
+}
+
+// The same outputs for the per-step kernel: the integer origins depend only
+// on Xref, which changes only at re-layouts (after which the general kernel
+// runs sphere_frame), so only the FP32 offset of the centre is renewed.
+// Lane `tl` < 3 of the sphere's team computes axis tl; lane 0 checks.
+__device__ __forceinline__ void sphere_offset(const Dem& D, int i, int tl, float& dmax, float& vmax, uint32_t& bad) {
+    if (tl < 3) {
+        const float* dx = reinterpret_cast<const float*>(&D.dX[i]);
+        const float* c = reinterpret_cast<const float*>(&D.dXc[i]);
+        const int* o = reinterpret_cast<const int*>(&D.org[i]);
+        double X = D.Xref[3 * i + tl] + (double)dx[tl] - (double)c[tl];
+        reinterpret_cast<float*>(&D.xf[i])[tl] = (float)(X - o[tl]);
+    }
+    if (tl == 0) {
+        float4 dx = D.dX[i], v = D.V[i];
+        float dd = sqrtf(dx.x * dx.x + dx.y * dx.y + dx.z * dx.z);
+        float vv = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+        if (!(dd == dd) || !(vv == vv) || isinf(dd) || isinf(vv)) bad |= ST_UNSTABLE;
+        else if (dd >= D.hard_disp) bad |= ST_SKIN;
+        dmax = fmaxf(dmax, dd);
+        vmax = fmaxf(vmax, vv);
+    }
 }
 
 // Warp reduction of the maxima and the status bits, one atomic each per warp
@@ -357,28 +381,27 @@ __global__ void __launch_bounds__(DSM_THREADS, 1) k_dem_step_dsm(Dem D) {
         cnt = D.nb_cnt[i];
     }
     // hydrodynamic drive: the mean of this and the previous step's exchange
-    // sums (the team's first thread sums the replicas, the team shares it)
-    float3 fa = zero, ta = zero;
-    if (have && tl == 0) {
-        double f[3] = {0.0, 0.0, 0.0}, t[3] = {0.0, 0.0, 0.0};
-        for (int r = 0; r < NREP; ++r)
-            for (int a = 0; a < 3; ++a) {
-                f[a] += D.Fh[3 * ((size_t)r * D.n + i) + a];
-                t[a] += D.Th[3 * ((size_t)r * D.n + i) + a];
-            }
-        fa = make_float3((float)(0.5 * (f[0] + D.Fh_prev[3 * i])), (float)(0.5 * (f[1] + D.Fh_prev[3 * i + 1])),
-                         (float)(0.5 * (f[2] + D.Fh_prev[3 * i + 2])));
-        ta = make_float3((float)(0.5 * (t[0] + D.Th_prev[3 * i])), (float)(0.5 * (t[1] + D.Th_prev[3 * i + 1])),
-                         (float)(0.5 * (t[2] + D.Th_prev[3 * i + 2])));
-        for (int a = 0; a < 3; ++a) {
-            D.Fh_prev[3 * i + a] = f[a];
-            D.Th_prev[3 * i + a] = t[a];
+    // sums.  The FP64 replica sums are split over the team: lane tl < 3
+    // sums force and torque component tl (same operations and order as one
+    // lane would), then the team shares them.
+    float hf = 0.f, ht = 0.f;
+    if (have && tl < 3) {
+        double f = 0.0, t = 0.0;
+        for (int r = 0; r < NREP; ++r) {
+            f += D.Fh[3 * ((size_t)r * D.n + i) + tl];
+            t += D.Th[3 * ((size_t)r * D.n + i) + tl];
         }
-        D.Fa[i] = make_float4(fa.x, fa.y, fa.z, 0.f);
-        D.Ta[i] = make_float4(ta.x, ta.y, ta.z, 0.f);
+        hf = (float)(0.5 * (f + D.Fh_prev[3 * i + tl]));
+        ht = (float)(0.5 * (t + D.Th_prev[3 * i + tl]));
+        D.Fh_prev[3 * i + tl] = f;
+        D.Th_prev[3 * i + tl] = t;
+        reinterpret_cast<float*>(&D.Fa[i])[tl] = hf;
+        reinterpret_cast<float*>(&D.Ta[i])[tl] = ht;
     }
-    fa = make_float3(__shfl_sync(full, fa.x, lead), __shfl_sync(full, fa.y, lead), __shfl_sync(full, fa.z, lead));
-    ta = make_float3(__shfl_sync(full, ta.x, lead), __shfl_sync(full, ta.y, lead), __shfl_sync(full, ta.z, lead));
+    const float3 fa = make_float3(__shfl_sync(full, hf, lead), __shfl_sync(full, hf, lead + 1),
+                                  __shfl_sync(full, hf, lead + 2));
+    const float3 ta = make_float3(__shfl_sync(full, ht, lead), __shfl_sync(full, ht, lead + 1),
+                                  __shfl_sync(full, ht, lead + 2));
     // this lane's neighbour entries tl + u TEAM, u < NBT
     int nj[NBT];
     float4 ndr[NBT];
@@ -456,7 +479,8 @@ __global__ void __launch_bounds__(DSM_THREADS, 1) k_dem_step_dsm(Dem D) {
     }
     float dmax = 0.f, vmax = 0.f;
     uint32_t bad = 0;
-    if (have && tl == 0) sphere_frame(D, i, dmax, vmax, bad);
+    __syncwarp();
+    if (have) sphere_offset(D, i, tl, dmax, vmax, bad);
     flush_maxima(D, dmax, vmax, bad);
 }
 
