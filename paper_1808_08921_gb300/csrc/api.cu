@@ -91,6 +91,7 @@ struct lbmdem_ctx {
     uint32_t nA = 0, nS = 0, nSpad = 0;
     DBuf<uint32_t> band_coord, band_count;
     DBuf<int4> band_cand;
+    DBuf<float> band_slack;
     uint32_t nband = 0;
     DBuf<uint32_t> surf_count, surf_off;
     DBuf<uint2> surf_link;
@@ -270,6 +271,8 @@ static Dem make_dem(lbmdem_ctx* c) {
     DevStats* s = c->st.p;
     D.status = &s->status;
     D.max_disp_bits = &s->max_disp_bits;
+    D.disp_layout_bits = &s->disp_layout_bits;
+    D.layout_fresh = &s->layout_fresh;
     D.max_vel_bits = &s->max_vel_bits;
     D.hard_disp = (float)c->hard;
     D.px = c->p.inlet == LBMDEM_X_PERIODIC;
@@ -442,11 +445,17 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
     }
     c->nband = nband;
     CK(c->band_cand.ensure(std::max<uint32_t>(nband, 1)));
+    CK(c->band_slack.ensure(std::max<uint32_t>(nband, 1)));
     if (int r = build_cells(c)) return r;
     BandCand BC{c->Xref.p, c->Rd.p, c->skin, c->grid, c->cell_start.p, c->cell_order.p,
-                c->band_coord.p, c->band_cand.p, nband, &c->st.p->status, c->band.p, nx, ny, nz};
+                c->band_coord.p, c->band_cand.p, c->band_slack.p, nband, &c->st.p->status, c->band.p, nx, ny, nz};
     launch_band_cand(BC, s);
     CK(cudaGetLastError());
+    // the owner map matches the layout positions only after the next map
+    // update: it re-tests every band node, later ones skip nodes whose slack
+    // exceeds the largest displacement since the layout
+    CK(cudaMemsetAsync(&c->st.p->disp_layout_bits, 0, sizeof(uint32_t), s));
+    CK(cudaMemsetAsync(&c->st.p->layout_fresh, 1, sizeof(uint32_t), s));
     // link lists, grouped by sphere (direction-major inside a sphere)
     int np = c->np;
     size_t ng = (size_t)std::max(np, 1) * (Q - 1);
@@ -559,7 +568,7 @@ static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
     if (c->lbm) {
         Lat L = make_lat(c);
         PartView P = make_part(c);
-        Band B{c->band_coord.p, c->band_cand.p, c->nband};
+        Band B{c->band_coord.p, c->band_cand.p, c->band_slack.p, c->nband};
         FlipBuf F{c->flip_rec.p, c->flip_scratch.p, c->flip_valid.p, c->flip_cap};
         if (tm) record_pair_begin(c, 2, e);
         launch_map_update(L, P, B, F, c->st.p, parity == 1, parity, s);

@@ -252,13 +252,13 @@ struct DevStats {
     uint32_t nflip[2];    // conversions queued this step (double-buffered by step parity)
     uint32_t max_disp_bits;  // float bits of max |dX| (non-negative)
     uint32_t max_vel_bits;   // float bits of max |V|
-    uint32_t pad0;
+    uint32_t disp_layout_bits;  // float bits of max |dX| seen since the layout build
     unsigned long long t;    // steps begun (the map update counts each step first; between
                              // steps it equals the completed steps)
     unsigned long long flips_total;
     double mon[6];           // sum rho, sum rho u, max|u|, step
     uint32_t max_u_bits;
-    uint32_t pad1;
+    uint32_t layout_fresh;   // 1 from a layout build until the first step's DEM
 };
 
 }  // namespace lbmdem

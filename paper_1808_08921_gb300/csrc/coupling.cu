@@ -239,6 +239,12 @@ __global__ void k_map_band(MapArgs A) {
         }
     }
     if (k >= A.band.n) return;
+    // a node farther from every candidate surface (at the layout) than any
+    // sphere has moved since keeps its owner
+    if (!A.st->layout_fresh) {
+        const float moved = __uint_as_float(A.st->disp_layout_bits);
+        if (A.band.slack[k] > moved + 1e-5f * (1.f + moved)) return;
+    }
     const Lat& L = A.L;
     int x, y, z;
     unpack_coord(A.band.coord[k], x, y, z);

@@ -52,7 +52,10 @@ constexpr int TEAM = 4;  // threads per sphere: they share its neighbour list
 // dX_i; dr = the entry's reference separation (w: (R_i + R_j)^2 - |xyz|^2).
 // Updates the history h (force on i) and adds the force and torque on i.
 // The arithmetic is mirror-exact: sphere j, evaluating the same pair,
-// obtains exactly the negative force.
+// obtains exactly the negative force.  Square roots and divisions use the
+// hardware approximations (reciprocal square root, fast divide; a few ulp):
+// deterministic functions of symmetric operands, so exactness of the pair
+// is kept.
 __device__ __forceinline__ void pair_contact(const Dem& D, float Ri, float Rj, float3 dl, float4 dr, float3 vi,
                                              float3 wi, float3 vj, float3 wj, float dt_inc, float4& h, float3& F,
                                              float3& T) {
@@ -64,12 +67,14 @@ __device__ __forceinline__ void pair_contact(const Dem& D, float Ri, float Rj, f
         h = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
-    float dist = sqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-    float delta = qd / (cut + dist);
-    float idist = 1.0f / dist;  // |d| is the same for both spheres: n stays mirror-exact
+    float d2 = d.x * d.x + d.y * d.y + d.z * d.z;
+    float idist = rsqrtf(d2);
+    float dist = d2 * idist;
+    float delta = __fdividef(qd, cut + dist);
     float3 n = make_float3(d.x * idist, d.y * idist, d.z * idist);
-    float Rs = Ri * Rj / (Ri + Rj);
-    float sq = sqrtf(Rs * delta);
+    float Rs = __fdividef(Ri * Rj, Ri + Rj);
+    float rd = Rs * delta;
+    float sq = rd * rsqrtf(rd);
     float fn = D.kn * sq * delta;
     float ai = Ri - 0.5f * delta, aj = Rj - 0.5f * delta;
     float3 ri = make_float3(ai * n.x, ai * n.y, ai * n.z);
@@ -85,7 +90,7 @@ __device__ __forceinline__ void pair_contact(const Dem& D, float Ri, float Rj, f
     float ftm2 = ft.x * ft.x + ft.y * ft.y + ft.z * ft.z;
     float cap = D.mu * fn;
     if (ftm2 > cap * cap) {  // |F_t| > mu |F_n|, compared in squares
-        float sc = cap / sqrtf(ftm2);
+        float sc = cap * rsqrtf(ftm2);
         ft = make_float3(ft.x * sc, ft.y * sc, ft.z * sc);
     }
     h = make_float4(ft.x, ft.y, ft.z, 0.f);
@@ -228,7 +233,10 @@ __device__ __forceinline__ void flush_maxima(const Dem& D, float dmax, float vma
         bad |= __shfl_xor_sync(full, bad, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        if (dmax > 0.f) atomicMax(D.max_disp_bits, __float_as_uint(dmax));
+        if (dmax > 0.f) {
+            atomicMax(D.max_disp_bits, __float_as_uint(dmax));
+            atomicMax(D.disp_layout_bits, __float_as_uint(dmax));
+        }
         if (vmax > 0.f) atomicMax(D.max_vel_bits, __float_as_uint(vmax));
         if (bad) atomicOr(D.status, bad);
     }
@@ -240,6 +248,7 @@ __global__ void k_dem_step(Dem D, int init_only) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int team = tid / TEAM, tl = tid % TEAM, nteams = nth / TEAM;
     const int iters = (D.n + nteams - 1) / nteams;  // uniform: shuffles stay converged
+    if (!init_only && tid == 0) *D.layout_fresh = 0u;  // this step's map update is done
     if (init_only) {
         for (int i = tid; i < D.n; i += nth) {
             D.dXb[i] = D.dX[i];
@@ -354,6 +363,7 @@ constexpr int NBT = 3;
 __global__ void __launch_bounds__(DSM_THREADS, 1) k_dem_step_dsm(Dem D) {
     extern __shared__ float4 xchg[];  // [2 substep parities][3: dX, Vh, Wh][spc]
     cg::cluster_group cl = cg::this_cluster();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *D.layout_fresh = 0u;  // this step's map update is done
     const int spc = blockDim.x / TEAM;
     const int tl = threadIdx.x % TEAM, ls = threadIdx.x / TEAM;
     const int i = blockIdx.x * spc + ls;
@@ -740,7 +750,13 @@ void launch_nb_build(const NbBuild& B, cudaStream_t s) {
 }
 
 // Spheres whose surface may reach a band node before the next re-layout
-// (|y - Xref| < R + skin, all images), ascending, at most 4.
+// (|y - Xref| < R + skin, all images), ascending, at most 4, and the node's
+// slack: its distance to the nearest candidate surface.  The owner of the
+// node is a function of the candidates' inside tests (and, inside two or
+// more spheres, of their distance ratios), so it cannot change while every
+// sphere stays closer than the slack to its layout position; a node inside
+// two or more candidates, or a boundary-plane node, is flagged 0 (always
+// re-tested) or never changes (planes stay fluid) respectively.
 __global__ void k_band_cand(BandCand B) {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= B.n) return;
@@ -756,7 +772,8 @@ __global__ void k_band_cand(BandCand B) {
     double L[3] = {G.L.x, G.L.y, G.L.z};
     int per[3] = {G.px, 1, 1};
     int c4[4] = {-1, -1, -1, -1};
-    int nfound = 0;
+    int nfound = 0, ninside = 0;
+    double slack = 1e30;
     for (int dx = -1; dx <= 1; ++dx) {
         int ux = ci[0] + dx, wx = ux;
         if (per[0]) wx = floormod(ux, nc[0]);
@@ -779,6 +796,8 @@ __global__ void k_band_cand(BandCand B) {
                     }
                     double r = B.R[p] + B.skin;
                     if (d2 >= r * r) continue;
+                    slack = fmin(slack, fabs(sqrt(d2) - B.R[p]));
+                    ninside += d2 < B.R[p] * B.R[p];
                     if (nfound >= 4) {
                         atomicOr(B.status, ST_CAPACITY);
                         continue;
@@ -795,6 +814,9 @@ __global__ void k_band_cand(BandCand B) {
         }
     }
     B.cand[k] = make_int4(c4[0], c4[1], c4[2], c4[3]);
+    if (ninside >= 2) slack = 0.0;
+    if (!G.px && (x == 0 || x == B.nx - 1)) slack = 1e30;  // inlet/outlet planes stay fluid
+    B.slack[k] = (float)slack;
     if (B.band_dense) B.band_dense[((size_t)x * B.ny + y) * B.nz + z] = nfound >= 2 ? 2 : 1;
 }
 

@@ -61,6 +61,7 @@ struct LinkLists {
 struct Band {
     const uint32_t* coord;  // packed x, y, z
     const int4* cand;       // up to 4 sphere indices, ascending, -1 padded
+    const float* slack;     // distance to the nearest candidate surface at the layout (0: always re-test)
     uint32_t n;
 };
 
@@ -117,6 +118,8 @@ struct Dem {
     float4* xf;
     uint32_t* status;
     uint32_t* max_disp_bits;
+    uint32_t* disp_layout_bits;
+    uint32_t* layout_fresh;
     uint32_t* max_vel_bits;
     float hard_disp;             // displacement at which the layout is invalid
     int px;

@@ -81,6 +81,7 @@ struct BandCand {
     const int* order;
     const uint32_t* coord;
     int4* cand;
+    float* slack;
     uint32_t n;
     uint32_t* status;
     uint8_t* band_dense;   // per lattice node: 1 = one candidate sphere, 2 = several
