@@ -261,4 +261,32 @@ struct DevStats {
     uint32_t layout_fresh;   // 1 from a layout build until the first step's DEM
 };
 
+// Programmatic dependent launch.  The kernels of a step are launched with
+// programmatic stream serialization (launch_pdl): such a kernel may be
+// scheduled while its predecessor on the stream is still running, and its
+// first statement, pdl_wait(), blocks until the predecessor grid has
+// completed and its memory operations are visible, so nothing is read or
+// written early.  pdl_trigger() in the predecessor lets the successor launch
+// once every block of the predecessor has executed it (blocks that exit
+// count as triggered), which hides the successor's launch and block
+// scheduling behind the predecessor's tail.  Both are no-ops for a kernel
+// launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(block, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 }  // namespace lbmdem

@@ -94,6 +94,8 @@ __device__ __forceinline__ bool owns_neighbour(const Lat& L, const PartView& P, 
 // of NREP accumulator copies of the sphere.
 template <int ST>
 __global__ void __launch_bounds__(256, 4) k_links(Lat L, PartView P, LinkLists B) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int K = LINK_CHUNKS;
     auto* f = pops<ST>(L);
     // warps in reverse order: the last spheres' nodes were collided last and
@@ -178,9 +180,9 @@ void launch_links(const Lat& L, const PartView& P, const LinkLists& B, cudaStrea
     if (B.nwarps == 0) return;
     uint64_t threads = (uint64_t)B.nwarps * 32;  // one warp per LINK_WARP links
     unsigned blocks = (unsigned)((threads + 255) / 256);
-    if (L.st == 0) k_links<0><<<blocks, 256, 0, s>>>(L, P, B);
-    else if (L.st == 1) k_links<1><<<blocks, 256, 0, s>>>(L, P, B);
-    else k_links<2><<<blocks, 256, 0, s>>>(L, P, B);
+    if (L.st == 0) launch_pdl(k_links<0>, blocks, 256, s, L, P, B);
+    else if (L.st == 1) launch_pdl(k_links<1>, blocks, 256, s, L, P, B);
+    else launch_pdl(k_links<2>, blocks, 256, s, L, P, B);
 }
 
 // ------------------------------------------------------------ map update
@@ -211,6 +213,7 @@ struct MapArgs {
 };
 
 __global__ void k_map_band(MapArgs A) {
+    pdl_trigger();  // launched normally: its predecessors are the DEM and the boundary branch
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0) {
         A.st->nflip[A.par ^ 1] = 0;
@@ -329,6 +332,8 @@ __global__ void k_map_band(MapArgs A) {
 constexpr int MAP_THREADS = 384;  // >= 19 * 19
 template <int ST>
 __global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
+    pdl_wait();
+    pdl_trigger();
     const Lat& L = A.L;
     __shared__ float sg[Q * Q];
     __shared__ float srho[Q];
@@ -431,6 +436,8 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
 __device__ void map_commit_one(const MapArgs& A, uint32_t k);
 
 __global__ void k_map_commit(MapArgs A) {
+    pdl_wait();
+    pdl_trigger();
     uint32_t nf = min(A.st->nflip[A.par], A.F.cap);
     uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
     if (t0 == 0) atomicAdd(&A.st->flips_total, (unsigned long long)nf);
@@ -465,6 +472,8 @@ __device__ void map_commit_one(const MapArgs& A, uint32_t k) {
 // node j = t / 19 back with the new map.
 template <int ST>
 __global__ void __launch_bounds__(MAP_THREADS) k_map_scatter(MapArgs A) {
+    pdl_wait();
+    pdl_trigger();
     const Lat L = A.L;
     const uint32_t nf = min(A.st->nflip[A.par], A.F.cap);
     const int t = threadIdx.x, j = t / Q, m = t % Q;
@@ -492,13 +501,13 @@ void launch_map_update(const Lat& L, const PartView& P, const Band& band, const 
     if (band.n == 0) return;
     // the queued count is read on the device: fixed grids stride over it
     const unsigned grid = 2 * 152;
-    if (L.st == 0) k_map_gather_convert<0><<<grid, MAP_THREADS, 0, s>>>(A);
-    else if (L.st == 1) k_map_gather_convert<1><<<grid, MAP_THREADS, 0, s>>>(A);
-    else k_map_gather_convert<2><<<grid, MAP_THREADS, 0, s>>>(A);
-    k_map_commit<<<grid, 256, 0, s>>>(A);
-    if (L.st == 0) k_map_scatter<0><<<grid, MAP_THREADS, 0, s>>>(A);
-    else if (L.st == 1) k_map_scatter<1><<<grid, MAP_THREADS, 0, s>>>(A);
-    else k_map_scatter<2><<<grid, MAP_THREADS, 0, s>>>(A);
+    if (L.st == 0) launch_pdl(k_map_gather_convert<0>, grid, MAP_THREADS, s, A);
+    else if (L.st == 1) launch_pdl(k_map_gather_convert<1>, grid, MAP_THREADS, s, A);
+    else launch_pdl(k_map_gather_convert<2>, grid, MAP_THREADS, s, A);
+    launch_pdl(k_map_commit, grid, 256, s, A);
+    if (L.st == 0) launch_pdl(k_map_scatter<0>, grid, MAP_THREADS, s, A);
+    else if (L.st == 1) launch_pdl(k_map_scatter<1>, grid, MAP_THREADS, s, A);
+    else launch_pdl(k_map_scatter<2>, grid, MAP_THREADS, s, A);
 }
 
 }  // namespace lbmdem

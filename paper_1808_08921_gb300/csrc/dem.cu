@@ -362,6 +362,7 @@ constexpr int NBT = 3;
 
 __global__ void __launch_bounds__(DSM_THREADS, 1) k_dem_step_dsm(Dem D) {
     extern __shared__ float4 xchg[];  // [2 substep parities][3: dX, Vh, Wh][spc]
+    pdl_wait();
     cg::cluster_group cl = cg::this_cluster();
     if (blockIdx.x == 0 && threadIdx.x == 0) *D.layout_fresh = 0u;  // this step's map update is done
     const int spc = blockDim.x / TEAM;
@@ -534,7 +535,7 @@ void launch_dem_step(const Dem& D, bool init_only, cudaStream_t s) {
     cudaGetDevice(&dev);
     if (init_only) probe_dsm(dev);
     long long need = (long long)TEAM * (D.n > 0 ? D.n : 1);
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
@@ -555,6 +556,10 @@ void launch_dem_step(const Dem& D, bool init_only, cudaStream_t s) {
         cfg.blockDim = dim3(T, 1, 1);
         cfg.dynamicSmemBytes = 6 * (T / TEAM) * sizeof(float4);
         attr[0].val.clusterDim.x = C;
+        // programmatic dependency on the link kernel (pdl_wait first)
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.numAttrs = 2;
         cudaLaunchKernelEx(&cfg, k_dem_step_dsm, D);
         return;
     }

@@ -155,6 +155,8 @@ __device__ __forceinline__ void mon_flush(const MonAcc& a, const Mon& mon, bool 
 // processed harmlessly (their slots are never read while they are solid).
 template <bool MON, int ST>
 __global__ void __launch_bounds__(256) k_collide_even(Lat L, Mon mon) {
+    pdl_wait();
+    pdl_trigger();
     auto* f = pops<ST>(L);
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t i0 = t * 4u;
@@ -228,6 +230,8 @@ struct LineProbe {
 // reads and writes the same 19 locations, so the update is in place.
 template <bool MON, int ST>
 __global__ void __launch_bounds__(256, 4) k_collide_odd(Lat L, Mon mon) {
+    pdl_wait();
+    pdl_trigger();
     auto* f = pops<ST>(L);
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     MonAcc a = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -317,15 +321,15 @@ static void launch_collide_st(const Lat& L, const Mon& mon, bool odd, bool monit
         uint32_t threads = (L.nS + 3) / 4;
         uint32_t blocks = (threads + tile - 1) / tile;
         if (monitor)
-            k_collide_even<true, ST><<<blocks, tile, 0, s>>>(L, mon);
+            launch_pdl(k_collide_even<true, ST>, blocks, tile, s, L, mon);
         else
-            k_collide_even<false, ST><<<blocks, tile, 0, s>>>(L, mon);
+            launch_pdl(k_collide_even<false, ST>, blocks, tile, s, L, mon);
     } else {
         uint32_t blocks = (L.nS + tile - 1) / tile;
         if (monitor)
-            k_collide_odd<true, ST><<<blocks, tile, 0, s>>>(L, mon);
+            launch_pdl(k_collide_odd<true, ST>, blocks, tile, s, L, mon);
         else
-            k_collide_odd<false, ST><<<blocks, tile, 0, s>>>(L, mon);
+            launch_pdl(k_collide_odd<false, ST>, blocks, tile, s, L, mon);
     }
 }
 
