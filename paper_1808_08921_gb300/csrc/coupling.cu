@@ -115,6 +115,15 @@ __global__ void __launch_bounds__(256, 4) k_links(Lat L, PartView P, LinkLists B
     bool on[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) on[k] = lk[k].x != NONE;
+    // the populations are loaded before the link is confirmed: a covered
+    // link node keeps its slots, so the load is in bounds, and its latency
+    // overlaps the fluid-bit and ownership checks
+    float v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int op = kDir[(dirs >> (8 * k)) & 31u].op;
+        v[k] = on[k] ? to_f<ST>(f[(size_t)op * L.nSpad + lk[k].x], L.fsi) : 0.f;
+    }
     if (dirs & 0x8080808080808080ull) {  // some chunk holds flagged links
         uint32_t fb[K];
 #pragma unroll
@@ -127,12 +136,6 @@ __global__ void __launch_bounds__(256, 4) k_links(Lat L, PartView P, LinkLists B
             if (on[k] && (lk[k].y >> 24 & 1u))
                 on[k] = owns_neighbour(L, P, p, lk[k].y, kDir[(dirs >> (8 * k)) & 31u], xf, R2);
         }
-    }
-    float v[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int op = kDir[(dirs >> (8 * k)) & 31u].op;
-        v[k] = on[k] ? to_f<ST>(f[(size_t)op * L.nSpad + lk[k].x], L.fsi) : 0.f;
     }
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
