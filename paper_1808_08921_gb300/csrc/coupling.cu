@@ -330,8 +330,9 @@ __global__ void k_map_band(MapArgs A) {
 
 // One block per queued node (grid-stride over the queue): thread t < 361
 // gathers population m = t % 19 of node j = t / 19 with the old map, where
-// j < 18 is the neighbour x + c_j and j = 18 the node itself; the block's
-// first thread then applies the conversion.
+// j < 18 is the neighbour x + c_j and j = 18 the node itself; thread 361,
+// idle during the gather, loads the sphere's state and the node's offset
+// from its centre meanwhile and then applies the conversion.
 constexpr int MAP_THREADS = 384;  // >= 19 * 19
 template <int ST>
 __global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
@@ -343,11 +344,25 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
     __shared__ int sv[Q];
     const uint32_t nf = min(A.st->nflip[A.par], A.F.cap);
     const int t = threadIdx.x, j = t / Q, m = t % Q;
+    constexpr int CT = Q * Q;  // the converting thread
     for (uint32_t w = blockIdx.x; w < nf; w += gridDim.x) {
         const Flip f = A.F.rec[w];
         int x, y, z;
         unpack_coord(f.coord, x, y, z);
         float* sc = A.F.scratch + (size_t)w * Q * Q;
+        const int o = f.old_owner, nw = f.new_owner;
+        const int ps = o != OWNER_FLUID ? o : nw;  // the sphere that gains or loses the node
+        double r[3] = {0.0, 0.0, 0.0};
+        float4 V = make_float4(0.f, 0.f, 0.f, 0.f), W = V;
+        if (t == CT && ps != OWNER_FLUID) {
+            double X0, X1, X2;
+            centre(A.P, ps, X0, X1, X2);
+            r[0] = node_offset(x, X0, L.nx, L.px);
+            r[1] = node_offset(y, X1, L.ny, 1);
+            r[2] = node_offset(z, X2, L.nz, 1);
+            V = A.P.V[ps];
+            W = A.P.W[ps];
+        }
         if (t < Q * Q) {
             bool valid = false;
             float g = 0.f;
@@ -374,7 +389,7 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
             srho[t] = L.rho_f + d;
         }
         __syncthreads();
-        if (t == 0) {
+        if (t == CT) {
             // mean density of the fluid neighbours (not the node itself)
             float rs = 0.f, rc = 0.f;
             for (int jj = 0; jj < Q - 1; ++jj) {
@@ -382,7 +397,6 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
                 rs += srho[jj];
                 rc += 1.f;
             }
-            int o = f.old_owner, nw = f.new_owner;
             if (o == OWNER_FLUID && nw != OWNER_FLUID) {
                 // covered: the sphere gains the node's momentum (Eq. 16)
                 const float* g = sg + 18 * Q;
@@ -392,10 +406,6 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
                     jm[1] += cy(mm) * (double)g[mm];
                     jm[2] += cz(mm) * (double)g[mm];
                 }
-                double X0, X1, X2;
-                centre(A.P, nw, X0, X1, X2);
-                double r[3] = {node_offset(x, X0, L.nx, L.px), node_offset(y, X1, L.ny, 1),
-                               node_offset(z, X2, L.nz, 1)};
                 atomicAdd(&A.P.Fh[3 * nw], jm[0]);
                 atomicAdd(&A.P.Fh[3 * nw + 1], jm[1]);
                 atomicAdd(&A.P.Fh[3 * nw + 2], jm[2]);
@@ -405,11 +415,6 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
             } else if (o != OWNER_FLUID && nw == OWNER_FLUID) {
                 // uncovered: equilibrium at rho_bar and the surface velocity (Eq. 17)
                 double rb = rc > 0.f ? (double)rs / (double)rc : (double)L.rho_f;
-                double X0, X1, X2;
-                centre(A.P, o, X0, X1, X2);
-                double r[3] = {node_offset(x, X0, L.nx, L.px), node_offset(y, X1, L.ny, 1),
-                               node_offset(z, X2, L.nz, 1)};
-                float4 V = A.P.V[o], W = A.P.W[o];
                 double vb[3] = {V.x + (W.y * r[2] - W.z * r[1]), V.y + (W.z * r[0] - W.x * r[2]),
                                 V.z + (W.x * r[1] - W.y * r[0])};
                 float rbf = (float)rb;
