@@ -403,6 +403,8 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
     if (nS64 >= 0xffffffe0ull) return fail(c, LBMDEM_ERR_INVALID_ARG, "lattice too large");
     uint32_t nS = (uint32_t)nS64;
     uint32_t nSpad = std::max<uint32_t>(32u, (nS + 31u) & ~31u);
+    if ((uint64_t)Q * nSpad >= (1ull << 32))  // the kernels address populations with 32-bit offsets
+        return fail(c, LBMDEM_ERR_INVALID_ARG, "lattice too large: %u stored nodes", nS);
     launch_words_bases(LA, nA, s);
     CK(c->coord.ensure(nSpad));
     CK(c->fbits.ensure(nSpad / 32));

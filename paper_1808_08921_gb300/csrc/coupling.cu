@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(256, 4) k_links(Lat L, PartView P, LinkLists B
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int op = kDir[(dirs >> (8 * k)) & 31u].op;
-        v[k] = on[k] ? to_f<ST>(f[(size_t)op * L.nSpad + lk[k].x], L.fsi) : 0.f;
+        v[k] = on[k] ? to_f<ST>(f[(uint32_t)op * L.nSpad + lk[k].x], L.fsi) : 0.f;
     }
     if (dirs & 0x8080808080808080ull) {  // some chunk holds flagged links
         uint32_t fb[K];
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256, 4) k_links(Lat L, PartView P, LinkLists B
         const uint32_t y = lk[k].y;
         const float rx = rel_f(y, 0), ry = rel_f(y, 8), rz = rel_f(y, 16);
         const float delta = a.x + (rx * a.y + ry * a.z + rz * a.w);
-        f[(size_t)d.op * L.nSpad + lk[k].x] = from_f<ST>(v[k] - delta, L.fs);
+        f[(uint32_t)d.op * L.nSpad + lk[k].x] = from_f<ST>(v[k] - delta, L.fs);
         const float q = 2.0f * v[k] - delta;
         const float qx = d.cx * q, qy = d.cy * q, qz = d.cz * q;
         acc[0] += qx;

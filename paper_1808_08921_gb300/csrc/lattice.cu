@@ -269,43 +269,47 @@ __global__ void __launch_bounds__(256, 4) k_collide_odd(Lat L, Mon mon) {
             nb[17] = l.at(zm);
         }
         if (hasp) {
-            LineProbe l(L, xp, y, z);
-            nb[0] = l.at(z);
-            nb[8] = l.at(zp);
-            nb[9] = l.at(zm);
+            {
+                LineProbe l(L, xp, y, z);
+                nb[0] = l.at(z);
+                nb[8] = l.at(zp);
+                nb[9] = l.at(zm);
+            }
             nb[6] = LineProbe(L, xp, yp, z).at(z);
             nb[7] = LineProbe(L, xp, ym, z).at(z);
         } else {
             nb[0] = nb[8] = nb[9] = nb[6] = nb[7] = NONE;
         }
         if (hasm) {
-            LineProbe l(L, xm, y, z);
-            nb[1] = l.at(z);
-            nb[12] = l.at(zp);
-            nb[13] = l.at(zm);
+            {
+                LineProbe l(L, xm, y, z);
+                nb[1] = l.at(z);
+                nb[12] = l.at(zp);
+                nb[13] = l.at(zm);
+            }
             nb[10] = LineProbe(L, xm, yp, z).at(z);
             nb[11] = LineProbe(L, xm, ym, z).at(z);
         } else {
             nb[1] = nb[12] = nb[13] = nb[10] = nb[11] = NONE;
         }
+        // 32-bit element offsets (19 nSpad < 2^32, checked at the layout)
         float g[Q];
 #pragma unroll
         for (int m = 0; m < Q - 1; ++m) {
             uint32_t s = nb[opp(m)];
-            g[m] = to_f<ST>(s != NONE ? f[(size_t)opp(m) * L.nSpad + s] : f[(size_t)m * L.nSpad + i], L.fsi);
+            const uint32_t off = s != NONE ? (uint32_t)opp(m) * L.nSpad + s : (uint32_t)m * L.nSpad + i;
+            g[m] = to_f<ST>(f[off], L.fsi);
         }
-        g[18] = to_f<ST>(f[(size_t)18 * L.nSpad + i], L.fsi);
+        g[18] = to_f<ST>(f[18u * L.nSpad + i], L.fsi);
         float drho, jx, jy, jz;
         bgk(g, L.tau_inv, L.rho_f, drho, jx, jy, jz);
 #pragma unroll
         for (int m = 0; m < Q - 1; ++m) {
             uint32_t d = nb[m];
-            if (d != NONE)
-                f[(size_t)m * L.nSpad + d] = from_f<ST>(g[m], L.fs);
-            else
-                f[(size_t)opp(m) * L.nSpad + i] = from_f<ST>(g[m], L.fs);
+            const uint32_t off = d != NONE ? (uint32_t)m * L.nSpad + d : (uint32_t)opp(m) * L.nSpad + i;
+            f[off] = from_f<ST>(g[m], L.fs);
         }
-        f[(size_t)18 * L.nSpad + i] = from_f<ST>(g[18], L.fs);
+        f[18u * L.nSpad + i] = from_f<ST>(g[18], L.fs);
         if (MON) mon_add(a, drho, jx, jy, jz, L.rho_f);
         if ((i >= mon.pA0 && i < mon.pA1) || (i >= mon.pB0 && i < mon.pB1)) {
             a.pdrho += drho;
