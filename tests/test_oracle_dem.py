@@ -11,6 +11,10 @@
 * Free flight is exact; a torque-free spinning sphere's quaternion follows
   the exact rotation; fixed spheres stay put; total momentum is conserved
   through a multi-sphere oblique frictional collision.
+* The dry granular chain of Section 3.2 (60 spheres compressed by 0.01 at
+  every contact, free ends): behind the rarefaction that runs in from each
+  end the spheres move at the simple-wave speed of the Hertz law,
+  (4/5) sqrt(1.5 k_n sqrt(R*)/m) delta_0^(5/4).
 """
 import math
 
@@ -146,3 +150,22 @@ def test_oblique_frictional_collisions_conserve_momentum():
     p0 = m * s.particles()["V"].sum(0)
     s.step(150)
     assert np.allclose(m * s.particles()["V"].sum(0), p0, atol=1e-12)
+
+
+def test_dry_chain_release_wave_speed():
+    R, n, d0 = 5.005, 60, 0.01
+    X = np.array([[i * (2 * R - d0), 6.0, 6.0] for i in range(1, n + 1)])
+    X[0, 0] = 10.001
+    w = workloads.Workload(name="chain", nx=620, ny=12, nz=12, tau=1.0, inlet=workloads.X_PERIODIC, X=X,
+                           R=np.full(n, R), fixed=np.zeros(n, np.uint8), E_p=10.0, nu_p=0.2, mu=0.0,
+                           dem_substeps=10, amplitude=0.0)
+    o = oracle.Oracle(w, lbm_on=False)
+    o.step(600)
+    V = o.particles()["V"]
+    o.close()
+    m = w.rho_p * 4 / 3 * math.pi * R ** 3
+    kn = 2 * w.E_p / (3 * (1 - w.nu_p ** 2))
+    v_th = 0.8 * math.sqrt(1.5 * kn * math.sqrt(R / 2) / m) * d0 ** 1.25
+    assert abs(-V[5, 0] / v_th - 1) < 5e-3 and abs(V[n - 6, 0] / v_th - 1) < 5e-3
+    # the rest of the motion is along the chain
+    assert np.abs(V[:, 1:]).max() < 1e-12
