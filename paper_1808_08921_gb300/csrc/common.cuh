@@ -210,7 +210,7 @@ struct PartView {
 // The link kernel spreads its atomics over NREP copies of each sphere's
 // force and torque accumulators (fewer same-address collisions); the DEM
 // kernel and the read-out sum the copies.
-constexpr int NREP = 8;
+constexpr int NREP = 4;
 
 // Exact "inside" test shared by painting and the map update: |y - X|^2 < R^2
 // in FP64 without contraction, X = Xref + dX (+ compensation).

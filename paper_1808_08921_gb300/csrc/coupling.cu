@@ -192,9 +192,12 @@ void launch_links(const Lat& L, const PartView& P, const LinkLists& B, cudaStrea
 
 // Current centre of sphere p in FP64 and the node's offset to it along one
 // axis, taken to the nearest periodic image and rounded once: (y + k L) - X.
+// The image count k is taken in FP32 (no FP64 division): it can differ from
+// the exact one only for a node about half a box from the centre, which is
+// outside every sphere and band (R + skin < L / 2), either image.
 __device__ __forceinline__ double node_offset(int y, double X, int Lax, int periodic) {
     if (!periodic) return (double)y - X;
-    double k = floor((X - (double)y) / (double)Lax + 0.5);
+    float k = floorf((float)(X - (double)y) / (float)Lax + 0.5f);
     return (double)(y + (int)k * Lax) - X;
 }
 
@@ -400,12 +403,14 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
             if (o == OWNER_FLUID && nw != OWNER_FLUID) {
                 // covered: the sphere gains the node's momentum (Eq. 16)
                 const float* g = sg + 18 * Q;
-                double jm[3] = {0, 0, 0};
+                float j0 = 0.f, j1 = 0.f, j2 = 0.f;
+#pragma unroll
                 for (int mm = 0; mm < Q; ++mm) {
-                    jm[0] += cx(mm) * (double)g[mm];
-                    jm[1] += cy(mm) * (double)g[mm];
-                    jm[2] += cz(mm) * (double)g[mm];
+                    j0 += cx(mm) * g[mm];
+                    j1 += cy(mm) * g[mm];
+                    j2 += cz(mm) * g[mm];
                 }
+                const double jm[3] = {j0, j1, j2};
                 atomicAdd(&A.P.Fh[3 * nw], jm[0]);
                 atomicAdd(&A.P.Fh[3 * nw + 1], jm[1]);
                 atomicAdd(&A.P.Fh[3 * nw + 2], jm[2]);
@@ -414,11 +419,12 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map_gather_convert(MapArgs A) {
                 atomicAdd(&A.P.Th[3 * nw + 2], r[0] * jm[1] - r[1] * jm[0]);
             } else if (o != OWNER_FLUID && nw == OWNER_FLUID) {
                 // uncovered: equilibrium at rho_bar and the surface velocity (Eq. 17)
-                double rb = rc > 0.f ? (double)rs / (double)rc : (double)L.rho_f;
-                double vb[3] = {V.x + (W.y * r[2] - W.z * r[1]), V.y + (W.z * r[0] - W.x * r[2]),
-                                V.z + (W.x * r[1] - W.y * r[0])};
-                float rbf = (float)rb;
-                float ux = (float)vb[0], uy = (float)vb[1], uz = (float)vb[2];
+                const float rbf = rc > 0.f ? rs / rc : L.rho_f;
+                const double rb = rbf;
+                const float r0 = (float)r[0], r1 = (float)r[1], r2 = (float)r[2];
+                const float ux = V.x + (W.y * r2 - W.z * r1), uy = V.y + (W.z * r0 - W.x * r2),
+                            uz = V.z + (W.x * r1 - W.y * r0);
+                const double vb[3] = {ux, uy, uz};
                 float uu15 = 1.5f * (ux * ux + uy * uy + uz * uz);
                 float* g = sc + 18 * Q;
                 for (int mm = 0; mm < Q; ++mm) {
