@@ -158,24 +158,44 @@ __global__ void __launch_bounds__(256, 4) k_links(Lat L, PartView P, LinkLists B
         acc[4] += rz * qx - rx * qz;
         acc[5] += rx * qy - ry * qx;
     }
+    // torque about the centre, per lane (the correction is linear)
+    acc[3] -= xf.y * acc[2] - xf.z * acc[1];
+    acc[4] -= xf.z * acc[0] - xf.x * acc[2];
+    acc[5] -= xf.x * acc[1] - xf.y * acc[0];
+    // transposing butterfly: at each of the first three levels a lane keeps
+    // half of its components and sends the other half, so the six sums (two
+    // zero pads) take 4 + 2 + 1 + 1 + 1 shuffles; lane l ends with the warp
+    // sum of component 4 b4 + 2 b3 + b2 (b = bits of l)
     const unsigned full = 0xffffffffu;
+    float s8[8] = {acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], 0.f, 0.f};
+    {
+        const bool up = lane & 16;
 #pragma unroll
-    for (int o = 16; o; o >>= 1)
+        for (int c = 0; c < 4; ++c) {
+            const float keep = up ? s8[c + 4] : s8[c], send = up ? s8[c] : s8[c + 4];
+            s8[c] = keep + __shfl_xor_sync(full, send, 16);
+        }
+    }
+    {
+        const bool up = lane & 8;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) acc[c] += __shfl_xor_sync(full, acc[c], o);
-    if (lane == 0) {
-        acc[3] -= xf.y * acc[2] - xf.z * acc[1];
-        acc[4] -= xf.z * acc[0] - xf.x * acc[2];
-        acc[5] -= xf.x * acc[1] - xf.y * acc[0];
-        size_t rep = (size_t)(w % NREP) * P.n + p;
-        double* F = P.Fh + 3 * rep;
-        double* T = P.Th + 3 * rep;
-        atomicAdd(F + 0, (double)acc[0]);
-        atomicAdd(F + 1, (double)acc[1]);
-        atomicAdd(F + 2, (double)acc[2]);
-        atomicAdd(T + 0, (double)acc[3]);
-        atomicAdd(T + 1, (double)acc[4]);
-        atomicAdd(T + 2, (double)acc[5]);
+        for (int c = 0; c < 2; ++c) {
+            const float keep = up ? s8[c + 2] : s8[c], send = up ? s8[c] : s8[c + 2];
+            s8[c] = keep + __shfl_xor_sync(full, send, 8);
+        }
+    }
+    {
+        const bool up = lane & 4;
+        const float keep = up ? s8[1] : s8[0], send = up ? s8[0] : s8[1];
+        s8[0] = keep + __shfl_xor_sync(full, send, 4);
+    }
+    s8[0] += __shfl_xor_sync(full, s8[0], 2);
+    s8[0] += __shfl_xor_sync(full, s8[0], 1);
+    const int comp = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    if ((lane & 3) == 0 && comp < 6) {
+        const size_t rep = (size_t)(w % NREP) * P.n + p;
+        double* dst = comp < 3 ? P.Fh + 3 * rep + comp : P.Th + 3 * rep + (comp - 3);
+        atomicAdd(dst, (double)s8[0]);
     }
 }
 
