@@ -49,6 +49,16 @@ __constant__ DirC kDir[Q - 1] = {
 #undef LBMDEM_DIR
 };
 
+// the same directions as 16-byte global entries {cx, cy, cz, opposite}: one
+// 128-bit load per chunk in the link kernel's main loop
+__device__ const float4 kDirV[Q - 1] = {
+#define LBMDEM_DIRV(m) {(float)cx(m), (float)cy(m), (float)cz(m), (float)opp(m)}
+    LBMDEM_DIRV(0),  LBMDEM_DIRV(1),  LBMDEM_DIRV(2),  LBMDEM_DIRV(3),  LBMDEM_DIRV(4),  LBMDEM_DIRV(5),
+    LBMDEM_DIRV(6),  LBMDEM_DIRV(7),  LBMDEM_DIRV(8),  LBMDEM_DIRV(9),  LBMDEM_DIRV(10), LBMDEM_DIRV(11),
+    LBMDEM_DIRV(12), LBMDEM_DIRV(13), LBMDEM_DIRV(14), LBMDEM_DIRV(15), LBMDEM_DIRV(16), LBMDEM_DIRV(17),
+#undef LBMDEM_DIRV
+};
+
 // the LINK_CHUNKS direction bytes of warp w, in one load
 __device__ __forceinline__ unsigned long long warp_chunk_dirs(const LinkLists& B, uint32_t w) {
     if (LINK_CHUNKS == 8) return *reinterpret_cast<const unsigned long long*>(B.chunk_dir + (size_t)w * 8);
@@ -121,7 +131,7 @@ __global__ void __launch_bounds__(256, 4) k_links(Lat L, PartView P, LinkLists B
     float v[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const int op = kDir[(dirs >> (8 * k)) & 31u].op;
+        const int op = (int)__ldg(&kDirV[(dirs >> (8 * k)) & 31u]).w;
         v[k] = on[k] ? to_f<ST>(f[(uint32_t)op * L.nSpad + lk[k].x], L.fsi) : 0.f;
     }
     if (dirs & 0x8080808080808080ull) {  // some chunk holds flagged links
@@ -141,7 +151,8 @@ __global__ void __launch_bounds__(256, 4) k_links(Lat L, PartView P, LinkLists B
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const uint32_t m = (dirs >> (8 * k)) & 31u;
-        const DirC d = kDir[m];
+        const float4 dv = __ldg(&kDirV[m]);
+        const DirC d = {dv.x, dv.y, dv.z, 0.f, (int)dv.w};
         const float4 a = ab[m];
         if (!on[k]) continue;
         const uint32_t y = lk[k].y;
