@@ -460,7 +460,7 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
     CK(cudaMemsetAsync(&c->st.p->layout_fresh, 1, sizeof(uint32_t), s));
     // link lists, grouped by sphere (direction-major inside a sphere)
     int np = c->np;
-    size_t ng = (size_t)std::max(np, 1) * (Q - 1);
+    size_t ng = (size_t)std::max(np, 1) * LINK_GROUPS;
     CK(c->surf_count.ensure(ng + 2));  // + the total before padding
     CK(c->surf_off.ensure(ng + 1));
     CK(cudaMemsetAsync(c->surf_count.p, 0, sizeof(uint32_t) * (ng + 2), s));

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256, 4) k_links(Lat L, PartView P, LinkLists B
         const int op = (int)__ldg(&kDirV[(dirs >> (8 * k)) & 31u]).w;
         v[k] = on[k] ? to_f<ST>(f[(uint32_t)op * L.nSpad + lk[k].x], L.fsi) : 0.f;
     }
-    if (dirs & 0x8080808080808080ull) {  // some chunk holds flagged links
+    if (dirs & 0xC0C0C0C0C0C0C0C0ull) {  // some chunk needs the fluid-bit or the ownership check
         uint32_t fb[K];
 #pragma unroll
         for (int k = 0; k < K; ++k)  // only a node inside a band can have been covered
@@ -143,8 +143,9 @@ __global__ void __launch_bounds__(256, 4) k_links(Lat L, PartView P, LinkLists B
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             on[k] = on[k] && ((fb[k] >> (lk[k].x & 31)) & 1u);
-            if (on[k] && (lk[k].y >> 24 & 1u))
-                on[k] = owns_neighbour(L, P, p, lk[k].y, kDir[(dirs >> (8 * k)) & 31u], xf, R2);
+            // a chunk of `maybe` links (whole chunks, so the branch is uniform)
+            if ((dirs >> (8 * k)) & 64u)
+                if (on[k]) on[k] = owns_neighbour(L, P, p, lk[k].y, kDir[(dirs >> (8 * k)) & 31u], xf, R2);
         }
     }
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};

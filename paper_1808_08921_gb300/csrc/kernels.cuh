@@ -29,14 +29,16 @@ struct BC {
 };
 
 // Link lists for the link kernel.  Links are grouped by (sphere, direction
-// m), each group padded to whole chunks of 32 records, and each sphere's
-// groups together padded to whole LINK_WARP records, so a warp walks
-// LINK_WARP / 32 chunks of one sphere, each chunk in one direction (one
-// record per lane and chunk):
+// m, maybe), each group padded to whole chunks of 32 records, and each
+// sphere's groups together padded to whole LINK_WARP records, so a warp
+// walks LINK_WARP / 32 chunks of one sphere, each chunk in one direction
+// (one record per lane and chunk) and either without or with only `maybe`
+// links:
 //   warp_p[w]    = sphere index
 //   chunk_dir[c] = direction m of chunk c (the solid neighbour is x + c_m),
-//                  | 128 when the chunk holds a flagged link; warp w owns
-//                  chunks w LINK_CHUNKS ... (w + 1) LINK_CHUNKS - 1
+//                  | 64 for a chunk of `maybe` links, | 128 when the chunk
+//                  holds an `in_band` link; warp w owns chunks
+//                  w LINK_CHUNKS ... (w + 1) LINK_CHUNKS - 1
 //   link[r]      = {cidx of the fluid node x,
 //                   (x - org) + 128 packed 8 bits per axis | maybe << 24 |
 //                   shared << 25 | in_band << 26}
@@ -48,6 +50,7 @@ struct BC {
 // read); every other link node stays fluid.  cidx == NONE pads.
 constexpr int LINK_WARP = 256;
 constexpr int LINK_CHUNKS = LINK_WARP / 32;  // chunks per warp
+constexpr int LINK_GROUPS = 2 * (Q - 1);     // groups per sphere: (direction m, maybe) -> 2 m + maybe
 static_assert(LINK_CHUNKS == 4 || LINK_CHUNKS == 8, "4 or 8 chunk directions per warp");
 
 struct LinkLists {

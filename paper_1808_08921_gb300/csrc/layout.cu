@@ -307,29 +307,30 @@ __global__ void k_surf_count(SurfArgs A) {
     int z0 = (int)ceil(A.X[3 * p + 2] - reach), z1 = (int)floor(A.X[3 * p + 2] + reach);
     int ey = y1 - y0 + 1, ez = z1 - z0 + 1;
     long long vol = (long long)(x1 - x0 + 1) * ey * ez;
-    __shared__ uint32_t cnt[Q - 1];
-    if (threadIdx.x < Q - 1) cnt[threadIdx.x] = 0;
+    __shared__ uint32_t cnt[LINK_GROUPS];
+    if (threadIdx.x < LINK_GROUPS) cnt[threadIdx.x] = 0;
     __syncthreads();
     for (long long t = threadIdx.x; t < vol; t += blockDim.x) {
         SurfNode sn;
         if (!surf_node(A, p, t, x0, y0, z0, ey, ez, sn)) continue;
-        uint32_t bits = sn.sure | sn.maybe;
-        for (int m = 0; m < Q - 1; ++m)
-            if (bits >> m & 1u) atomicAdd(&cnt[m], 1u);
+        for (int m = 0; m < Q - 1; ++m) {
+            if (sn.sure >> m & 1u) atomicAdd(&cnt[2 * m], 1u);
+            if (sn.maybe >> m & 1u) atomicAdd(&cnt[2 * m + 1], 1u);
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t tot = 0, raw = 0;
-        for (int m = 0; m < Q - 1; ++m) {
-            raw += cnt[m];
-            cnt[m] = (cnt[m] + 31u) / 32u * 32u;
-            tot += cnt[m];
+        for (int g = 0; g < LINK_GROUPS; ++g) {
+            raw += cnt[g];
+            cnt[g] = (cnt[g] + 31u) / 32u * 32u;
+            tot += cnt[g];
         }
         atomicAdd(A.nlink, raw);
-        cnt[Q - 2] += (tot + (LINK_WARP - 1)) / LINK_WARP * LINK_WARP - tot;
+        cnt[LINK_GROUPS - 1] += (tot + (LINK_WARP - 1)) / LINK_WARP * LINK_WARP - tot;
     }
     __syncthreads();
-    if (threadIdx.x < Q - 1) A.count[(size_t)p * (Q - 1) + threadIdx.x] = cnt[threadIdx.x];
+    if (threadIdx.x < LINK_GROUPS) A.count[(size_t)p * LINK_GROUPS + threadIdx.x] = cnt[threadIdx.x];
 }
 
 // fill in a deterministic order: per direction, chunks of blockDim nodes in
@@ -342,24 +343,23 @@ __global__ void k_surf_fill(SurfArgs A) {
     int z0 = (int)ceil(A.X[3 * p + 2] - reach), z1 = (int)floor(A.X[3 * p + 2] + reach);
     int ey = y1 - y0 + 1, ez = z1 - z0 + 1;
     long long vol = (long long)(x1 - x0 + 1) * ey * ez;
-    __shared__ uint32_t sh[Q - 1][33];
-    __shared__ uint32_t run[Q - 1];
-    if (threadIdx.x < Q - 1) run[threadIdx.x] = 0;
+    __shared__ uint32_t sh[LINK_GROUPS][33];
+    __shared__ uint32_t run[LINK_GROUPS];
+    if (threadIdx.x < LINK_GROUPS) run[threadIdx.x] = 0;
     __syncthreads();
     uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (long long t0 = 0; t0 < vol; t0 += blockDim.x) {
         long long t = t0 + threadIdx.x;
         SurfNode sn;
         bool ok = t < vol && surf_node(A, p, t, x0, y0, z0, ey, ez, sn);
-        uint32_t bits = ok ? (sn.sure | sn.maybe) : 0u;
-        uint32_t before[Q - 1];
-        for (int m = 0; m < Q - 1; ++m) {
-            unsigned bal = __ballot_sync(0xffffffffu, (bits >> m) & 1u);
-            before[m] = __popc(bal & ((1u << lane) - 1u));
-            if (lane == 0) sh[m][wid] = __popc(bal);
+        // group 2 m + 1 takes the `maybe` links of direction m, 2 m the others
+        uint32_t sure = ok ? sn.sure : 0u, maybe = ok ? sn.maybe : 0u;
+        for (int g = 0; g < LINK_GROUPS; ++g) {
+            unsigned bal = __ballot_sync(0xffffffffu, (((g & 1) ? maybe : sure) >> (g >> 1)) & 1u);
+            if (lane == 0) sh[g][wid] = __popc(bal);
         }
         __syncthreads();
-        if (threadIdx.x < Q - 1) {
+        if (threadIdx.x < LINK_GROUPS) {
             uint32_t s = 0;
             for (uint32_t k = 0; k < nwarp; ++k) {
                 uint32_t c = sh[threadIdx.x][k];
@@ -369,40 +369,44 @@ __global__ void k_surf_fill(SurfArgs A) {
             sh[threadIdx.x][32] = s;
         }
         __syncthreads();
-        if (bits) {
-            uint32_t rel = (uint32_t)(sn.ox + 128) | ((uint32_t)(sn.oy + 128) << 8) |
-                           ((uint32_t)(sn.oz + 128) << 16);
-            for (int m = 0; m < Q - 1; ++m) {
-                if (!(bits >> m & 1u)) continue;
-                size_t g = (size_t)p * (Q - 1) + m;
-                uint32_t pos = A.offset[g] + run[m] + sh[m][wid] + before[m];
-                A.link[pos] = make_uint2(sn.ci, rel | ((sn.maybe >> m & 1u) << 24) | ((sn.shared >> m & 1u) << 25) |
-                                                    ((uint32_t)sn.in_band << 26));
-            }
+        uint32_t rel = ok ? ((uint32_t)(sn.ox + 128) | ((uint32_t)(sn.oy + 128) << 8) |
+                             ((uint32_t)(sn.oz + 128) << 16))
+                          : 0u;
+        for (int g = 0; g < LINK_GROUPS; ++g) {
+            const int m = g >> 1;
+            const bool mine = (((g & 1) ? maybe : sure) >> m) & 1u;
+            unsigned bal = __ballot_sync(0xffffffffu, mine);
+            if (!mine) continue;
+            uint32_t before = __popc(bal & ((1u << lane) - 1u));
+            uint32_t pos = A.offset[(size_t)p * LINK_GROUPS + g] + run[g] + sh[g][wid] + before;
+            A.link[pos] = make_uint2(sn.ci, rel | ((uint32_t)(g & 1) << 24) | ((sn.shared >> m & 1u) << 25) |
+                                                ((uint32_t)sn.in_band << 26));
         }
         __syncthreads();
-        if (threadIdx.x < Q - 1) run[threadIdx.x] += sh[threadIdx.x][32];
+        if (threadIdx.x < LINK_GROUPS) run[threadIdx.x] += sh[threadIdx.x][32];
         __syncthreads();
     }
-    // pad every (sphere, direction) group to its chunks
-    for (int m = 0; m < Q - 1; ++m) {
-        size_t g = (size_t)p * (Q - 1) + m;
-        uint32_t base = A.offset[g], end = base + A.count[g];
-        for (uint32_t k = base + run[m] + threadIdx.x; k < end; k += blockDim.x) A.link[k] = make_uint2(NONE, 0u);
+    // pad every group to its chunks
+    for (int g = 0; g < LINK_GROUPS; ++g) {
+        size_t gi = (size_t)p * LINK_GROUPS + g;
+        uint32_t base = A.offset[gi], end = base + A.count[gi];
+        for (uint32_t k = base + run[g] + threadIdx.x; k < end; k += blockDim.x) A.link[k] = make_uint2(NONE, 0u);
     }
     __syncthreads();
-    // label the chunks with their direction (| 128 when a chunk holds a
-    // flagged link: maybe, shared or in_band) and tag the sphere's warps
-    for (int m = 0; m < Q - 1; ++m) {
-        size_t g = (size_t)p * (Q - 1) + m;
-        uint32_t base = A.offset[g], end = base + A.count[g];
+    // label the chunks with their direction (| 64 for a chunk of maybe
+    // links, | 128 when a chunk holds an in_band link) and tag the sphere's
+    // warps
+    for (int g = 0; g < LINK_GROUPS; ++g) {
+        size_t gi = (size_t)p * LINK_GROUPS + g;
+        uint32_t base = A.offset[gi], end = base + A.count[gi];
         for (uint32_t k = base / 32 + wid; k < end / 32; k += nwarp) {
-            uint32_t fl = __ballot_sync(0xffffffffu, ((A.link[32 * k + lane].y >> 24) & 7u) != 0u);
-            if (lane == 0) A.chunk_dir[k] = (uint8_t)(m | (fl ? 128 : 0));
+            uint32_t fl = __ballot_sync(0xffffffffu, ((A.link[32 * k + lane].y >> 26) & 1u) != 0u);
+            if (lane == 0) A.chunk_dir[k] = (uint8_t)((g >> 1) | ((g & 1) ? 64 : 0) | (fl ? 128 : 0));
         }
     }
-    uint32_t first = A.offset[(size_t)p * (Q - 1)];
-    uint32_t last = A.offset[(size_t)p * (Q - 1) + Q - 2] + A.count[(size_t)p * (Q - 1) + Q - 2];
+    uint32_t first = A.offset[(size_t)p * LINK_GROUPS];
+    uint32_t last = A.offset[(size_t)p * LINK_GROUPS + LINK_GROUPS - 1] +
+                    A.count[(size_t)p * LINK_GROUPS + LINK_GROUPS - 1];
     for (uint32_t k = first / LINK_WARP + threadIdx.x; k < last / LINK_WARP; k += blockDim.x) A.warp_p[k] = (uint32_t)p;
 }
 

@@ -36,8 +36,8 @@ struct SurfArgs {
     double skin;
     const int32_t* owner;   // map at layout time
     const uint8_t* band;    // band flags at layout time
-    uint32_t* count;        // [n * 18] links per (sphere, direction), padded to 32; the
-                            // last direction of a sphere also holds the padding to LINK_WARP
+    uint32_t* count;        // [n * LINK_GROUPS] links per (sphere, direction, maybe), padded
+                            // to 32; the last group of a sphere also holds the padding to LINK_WARP
     const uint32_t* offset; // exclusive scan of count
     uint2* link;
     uint32_t* warp_p;
