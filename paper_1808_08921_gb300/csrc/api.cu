@@ -89,9 +89,9 @@ struct lbmdem_ctx {
     DBuf<uint8_t> f, f2;  // populations, 4 or 2 bytes each
     DBuf<uint32_t> coord, fbits;
     uint32_t nA = 0, nS = 0, nSpad = 0;
-    DBuf<uint32_t> band_coord, band_count;
-    DBuf<int4> band_cand;
-    DBuf<float> band_slack;
+    DBuf<uint32_t> band_coord, band_count, band_coord2, slack_hist;
+    DBuf<int4> band_cand, band_cand2;
+    DBuf<float> band_slack, band_slack2;
     uint32_t nband = 0;
     DBuf<uint32_t> surf_count, surf_off;
     DBuf<uint2> surf_link;
@@ -453,6 +453,18 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
                 c->band_coord.p, c->band_cand.p, c->band_slack.p, nband, &c->st.p->status, c->band.p, nx, ny, nz};
     launch_band_cand(BC, s);
     CK(cudaGetLastError());
+    if (nband > 0) {  // band ordered by slack
+        CK(c->band_coord2.ensure(nband));
+        CK(c->band_cand2.ensure(nband));
+        CK(c->band_slack2.ensure(nband));
+        CK(c->slack_hist.ensure(SLACK_HIST));
+        launch_band_sort(c->band_coord.p, c->band_cand.p, c->band_slack.p, nband, c->skin, c->slack_hist.p,
+                         c->scan_tmp.p, c->band_coord2.p, c->band_cand2.p, c->band_slack2.p, s);
+        CK(cudaGetLastError());
+        c->band_coord.swap(c->band_coord2);
+        c->band_cand.swap(c->band_cand2);
+        c->band_slack.swap(c->band_slack2);
+    }
     // the owner map matches the layout positions only after the next map
     // update: it re-tests every band node, later ones skip nodes whose slack
     // exceeds the largest displacement since the layout

@@ -829,6 +829,40 @@ void launch_band_cand(const BandCand& B, cudaStream_t s) {
     if (B.n > 0) k_band_cand<<<(B.n + 255) / 256, 256, 0, s>>>(B);
 }
 
+// Band list ordered by slack (bucket sort, order inside a bucket arbitrary):
+// the nodes a step has to re-test -- slack up to the displacement since the
+// layout -- then form a prefix of the list and fill whole warps, and the
+// warps past it leave after one coalesced load.
+constexpr int SLACK_BUCKETS = 1024;
+static_assert(SLACK_HIST == SLACK_BUCKETS + 1, "bucket counts and the total");
+__device__ __forceinline__ int slack_bucket(float slack, float top) {
+    float b = slack * (float)SLACK_BUCKETS / top;
+    return b < (float)(SLACK_BUCKETS - 1) ? (int)b : SLACK_BUCKETS - 1;
+}
+__global__ void k_slack_hist(const float* slack, uint32_t n, float top, uint32_t* hist) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) atomicAdd(&hist[slack_bucket(slack[k], top)], 1u);
+}
+__global__ void k_slack_scatter(const uint32_t* coord, const int4* cand, const float* slack, uint32_t n, float top,
+                                uint32_t* next, uint32_t* coord2, int4* cand2, float* slack2) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint32_t pos = atomicAdd(&next[slack_bucket(slack[k], top)], 1u);
+    coord2[pos] = coord[k];
+    cand2[pos] = cand[k];
+    slack2[pos] = slack[k];
+}
+void launch_band_sort(const uint32_t* coord, const int4* cand, const float* slack, uint32_t n, double skin,
+                      uint32_t* hist, uint32_t* scan_tmp, uint32_t* coord2, int4* cand2, float* slack2,
+                      cudaStream_t s) {
+    if (n == 0) return;
+    const float top = (float)(2.0 * skin);  // band nodes lie within skin of a surface
+    cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (SLACK_BUCKETS + 1), s);
+    k_slack_hist<<<(n + 255) / 256, 256, 0, s>>>(slack, n, top, hist);
+    exclusive_scan(hist, hist, SLACK_BUCKETS + 1, scan_tmp, s);
+    k_slack_scatter<<<(n + 255) / 256, 256, 0, s>>>(coord, cand, slack, n, top, hist, coord2, cand2, slack2);
+}
+
 __global__ void k_rebase(double* Xref, float4* dX, float4* dXc, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;

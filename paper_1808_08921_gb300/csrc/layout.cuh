@@ -106,6 +106,10 @@ void launch_cells(const double* X, int n, const CellGrid& G, int* cell_of, int* 
                   int* fill, int* order, cudaStream_t s);
 void launch_nb_build(const NbBuild& B, cudaStream_t s);
 void launch_band_cand(const BandCand& B, cudaStream_t s);
+constexpr int SLACK_HIST = 1024 + 1;  // bucket counts (+ total) of launch_band_sort
+void launch_band_sort(const uint32_t* coord, const int4* cand, const float* slack, uint32_t n, double skin,
+                      uint32_t* hist, uint32_t* scan_tmp, uint32_t* coord2, int4* cand2, float* slack2,
+                      cudaStream_t s);
 void launch_rebase(double* Xref, float4* dX, float4* dXc, int n, cudaStream_t s);
 
 }  // namespace lbmdem
