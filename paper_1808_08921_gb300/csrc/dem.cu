@@ -362,9 +362,11 @@ constexpr int NBT = 3;
 
 __global__ void __launch_bounds__(DSM_THREADS, 1) k_dem_step_dsm(Dem D) {
     extern __shared__ float4 xchg[];  // [2 substep parities][3: dX, Vh, Wh][spc]
-    pdl_wait();
+    // Launched with a programmatic dependency on the link kernel: the
+    // sphere state and neighbour entries (last written by the previous
+    // step's DEM, long complete) are read before waiting for it; the
+    // exchange sums it writes, and every write of this kernel, come after.
     cg::cluster_group cl = cg::this_cluster();
-    if (blockIdx.x == 0 && threadIdx.x == 0) *D.layout_fresh = 0u;  // this step's map update is done
     const int spc = blockDim.x / TEAM;
     const int tl = threadIdx.x % TEAM, ls = threadIdx.x / TEAM;
     const int i = blockIdx.x * spc + ls;
@@ -391,6 +393,23 @@ __global__ void __launch_bounds__(DSM_THREADS, 1) k_dem_step_dsm(Dem D) {
         fixed = D.fixed[i] != 0;
         cnt = D.nb_cnt[i];
     }
+    // this lane's neighbour entries tl + u TEAM, u < NBT
+    int nj[NBT];
+    float4 ndr[NBT];
+    float3 nh[NBT];
+#pragma unroll
+    for (int u = 0; u < NBT; ++u) {
+        int k = tl + u * TEAM;
+        nj[u] = -1;
+        if (k < cnt) {
+            size_t e = (size_t)i * D.nbmax + k;
+            nj[u] = D.nb_j[e];
+            ndr[u] = D.nb_dref[e];
+            nh[u] = f3(D.nb_ft[e]);
+        }
+    }
+    pdl_wait();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *D.layout_fresh = 0u;  // this step's map update is done
     // hydrodynamic drive: the mean of this and the previous step's exchange
     // sums.  The FP64 replica sums are split over the team: lane tl < 3
     // sums force and torque component tl (same operations and order as one
@@ -413,21 +432,6 @@ __global__ void __launch_bounds__(DSM_THREADS, 1) k_dem_step_dsm(Dem D) {
                                   __shfl_sync(full, hf, lead + 2));
     const float3 ta = make_float3(__shfl_sync(full, ht, lead), __shfl_sync(full, ht, lead + 1),
                                   __shfl_sync(full, ht, lead + 2));
-    // this lane's neighbour entries tl + u TEAM, u < NBT
-    int nj[NBT];
-    float4 ndr[NBT];
-    float3 nh[NBT];
-#pragma unroll
-    for (int u = 0; u < NBT; ++u) {
-        int k = tl + u * TEAM;
-        nj[u] = -1;
-        if (k < cnt) {
-            size_t e = (size_t)i * D.nbmax + k;
-            nj[u] = D.nb_j[e];
-            ndr[u] = D.nb_dref[e];
-            nh[u] = f3(D.nb_ft[e]);
-        }
-    }
     for (int s = 0; s < D.K; ++s) {
         const int b = s & 1;
         float3 vh = zero, wh = zero;
@@ -775,6 +779,7 @@ __global__ void k_band_cand(BandCand B) {
     ci[2] = cell_axis(P[2], 0.0, G.h.z, G.nc.z, G.L.z, 1, kk[2]);
     int nc[3] = {G.nc.x, G.nc.y, G.nc.z};
     double L[3] = {G.L.x, G.L.y, G.L.z};
+    const double iL[3] = {1.0 / G.L.x, 1.0 / G.L.y, 1.0 / G.L.z};  // once per node, not per candidate
     int per[3] = {G.px, 1, 1};
     int c4[4] = {-1, -1, -1, -1};
     int nfound = 0, ninside = 0;
@@ -796,7 +801,7 @@ __global__ void k_band_cand(BandCand B) {
                     double d2 = 0;
                     for (int q = 0; q < 3; ++q) {
                         double d = P[q] - B.X[3 * p + q];
-                        if (per[q]) d -= L[q] * floor(d / L[q] + 0.5);
+                        if (per[q]) d -= L[q] * floor(d * iL[q] + 0.5);
                         d2 += d * d;
                     }
                     double r = B.R[p] + B.skin;
