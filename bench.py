@@ -110,12 +110,22 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def _code_only(text):
+    """C/CUDA source without comments and whitespace (the sources hold no
+    string literal with a comment marker)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return re.sub(r"\s+", "", text)
+
+
 def _kernel_hash():
-    """Hash of the CUDA sources: a profile is valid only for the code it measured."""
+    """Hash of the CUDA sources' code (comments and layout excluded): a
+    profile is valid only for the code it measured."""
     import glob
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_1808_08921_gb300", "csrc", "*.cu*"))):
-        h.update(open(f, "rb").read())
+        h.update(_code_only(open(f).read()).encode())
     return h.hexdigest()[:16]
 
 

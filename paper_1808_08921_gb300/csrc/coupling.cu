@@ -1,9 +1,10 @@
 // coupling.cu -- fluid-solid coupling (Section 2.3).
 //
 //  * k_links: walks each sphere's link lists (one warp per LINK_WARP links of
-//    one sphere, in chunks of 32 links of one direction).  For every fluid node x and direction d whose
-//    neighbour x + c_d belongs to the sphere, slot opp(d) of x holds the
-//    post-collision value f~_d(x) (AA layout, either parity); it is replaced
+//    one sphere, in chunks of 32 links of one direction).  For every fluid
+//    node x and direction d whose neighbour x + c_d belongs to the sphere,
+//    slot opp(d) of x holds the post-collision value f~_d(x) (AA layout,
+//    either parity); it is replaced
 //    by the bounced value f~_d - 6 w_d rho_f c_d . V_b (Eq. 14, moving wall
 //    with V_b = V + Omega x (x_b - X), x_b = x + c_d / 2), and the link force
 //    c_d (f~_d + f_bounced - 2 w_d rho_f) (Eq. 15, counted about the rest
@@ -11,8 +12,10 @@
 //    stored as deviations from w_d rho_f this is c_d (2 g~_d - delta)) and
 //    its torque (Eq. 19) are summed by warp shuffles, then one FP64 atomic
 //    per warp per component.
-//  * map update: every node within `skin` of a sphere surface is re-tested
-//    against the current sphere positions (where spheres overlap, the one
+//  * map update: the nodes within `skin` of a sphere surface (the band) are
+//    re-tested against the current sphere positions -- after a layout all of
+//    them, later only those no farther from a candidate surface than the
+//    largest displacement since the layout -- (where spheres overlap, the one
 //    with the smallest |x - X|^2 / R^2 owns the node, the lowest index on a
 //    tie; the inlet/outlet planes stay fluid).  Changed nodes are
 //    queued; for each, the natural populations of the node and its 18
