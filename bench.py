@@ -13,12 +13,14 @@ groups, the algorithmic bytes per launch (collide+stream, both AA parities:
 152 B per fluid node, 19 FP32 populations read and written; links: 8 B per
 link record, one population read and the bounced value written) over the
 group's mean launch time, taken with CUDA events around every launch inside
-the timed region; `roofline` is the one with the longest launches, and
-`step_roofline` is the whole coupled step at 152 B per fluid node.
+the captured graphs during a second window of K steps that follows the
+headline window (those event nodes slow the step, so the headline `value`
+is timed without them); `roofline` is the one with the longest launches,
+and `step_roofline` is the whole coupled step at 152 B per fluid node.
 `e2e` times the same workload through the C ABI from host buffers:
 set_packing (host -> device, the layout build included), the K steps, and
-the read-back of the sphere state (device -> host).  `cpu_baseline` times the FP64 oracle on a few steps of the
-same workload on the host cores.  Multi-GPU (torchrun): every rank runs its
+the read-back of the sphere state (device -> host).  `cpu_baseline` times
+the FP64 oracle on a few steps of the same workload on the host cores.  Multi-GPU (torchrun): every rank runs its
 own column (independent problems, no collective), value = all ranks' fluid
 updates / the slowest rank's time.
 """
