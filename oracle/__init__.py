@@ -8,4 +8,5 @@ Parity pins live in tests/test_oracle_*.py.  Functions whose result the
 paper and mathematics do not fix beyond those pins are marked in the
 docstrings below.
 """
-from .oracle import Oracle, build, lattice, equilibrium, collide_node, pressure_face, pair_force  # noqa: F401
+from .oracle import (Oracle, build, lattice, equilibrium, collide_node, pressure_face, pair_force,  # noqa: F401
+                     set_threads, threads)

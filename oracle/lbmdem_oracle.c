@@ -46,6 +46,19 @@
  * wall) before the inlet/outlet overwrite them; zero-gradient outlet copies
  * the unknown populations from the upstream node when that node is fluid.
  *
+ * Threads (OpenMP, when compiled with it): the lattice loops run over
+ * x-planes in parallel and the contact search over the lower-index sphere
+ * of each pair.  Every floating-point sum has a fixed order whatever the
+ * thread count: link forces and torques (Eqs. 18-19) are summed per
+ * x-plane, then plane by plane in x order; pair contact forces are
+ * evaluated in parallel and added to the spheres in the serial pair order.
+ * One thread or many give bit-identical results.
+ *
+ * orc_set_link_form(s, 1) switches the link momentum to the literal Eq. 15,
+ * c_d (f~_d + f_d*), so that the tests can pin the rest-state reading
+ * against it (the two differ only by 2 w_d rho_f c_d summed over the links,
+ * which vanishes over the closed staircase of a fully wetted sphere).
+ *
  * Parity pins (tests/test_oracle_*.py): equilibrium moments, BGK
  * conservation, exact streaming shifts, Zou-He moment identities, mass
  * conservation with static spheres in a closed box, y/z momentum balance
@@ -55,6 +68,9 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -91,6 +107,28 @@ typedef struct {
     int n, cap;
 } hist_list;
 
+/* one sphere's link force and torque summed over one x-plane */
+typedef struct {
+    int p;
+    double F[3], T[3];
+} plane_sum;
+
+typedef struct {
+    plane_sum* e;
+    int n, cap;
+} plane_list;
+
+/* one pair contact found from the lower-index sphere i (Eqs. 11-12) */
+typedef struct {
+    int j;
+    double F[3], ti[3], tj[3];
+} pair_hit;
+
+typedef struct {
+    pair_hit* e;
+    int n, cap;
+} pair_list;
+
 struct orc_sim {
     orc_params p;
     long N;
@@ -117,6 +155,9 @@ struct orc_sim {
     double* trace;
     long long trace_len, trace_cap;
     int have_packing;
+    int link_literal;       /* 1: link momentum c_d (f~_d + f_d*) as printed in Eq. 15 */
+    plane_list* plane_acc;  /* [nx] link sums of each x-plane */
+    pair_list* pairs;       /* [np] contacts found from each lower-index sphere */
 };
 
 static inline long nidx(const orc_sim* s, int x, int y, int z) {
@@ -304,15 +345,28 @@ static void hist_remove(hist_list* h, hist_t* e) {
     h->n--;
 }
 
+static pair_hit* pair_push(pair_list* l) {
+    if (l->n == l->cap) {
+        l->cap = l->cap ? 2 * l->cap : 8;
+        l->e = (pair_hit*)realloc(l->e, sizeof(pair_hit) * l->cap);
+    }
+    return &l->e[l->n++];
+}
+
 /* All pairs, all periodic images (a sphere may touch several images of the
- * same neighbour when the box is narrow). */
+ * same neighbour when the box is narrow).  Pass 1 evaluates every pair
+ * (i < j) from sphere i, which alone owns the tangential history of its
+ * pairs (in parallel over i); pass 2 adds the pair forces to both spheres in
+ * the order i, j, image (serially, so the sums do not depend on threads). */
 static void contacts(orc_sim* s, double dt) {
     int np = s->np;
     double L[3] = {s->p.nx, s->p.ny, s->p.nz};
     int per[3] = {s->px, 1, 1};
-    memset(s->Fc, 0, sizeof(double) * 3 * np);
-    memset(s->Tc, 0, sizeof(double) * 3 * np);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
     for (int i = 0; i < np; ++i) {
+        s->pairs[i].n = 0;
         for (int j = i + 1; j < np; ++j) {
             double cut = s->R[i] + s->R[j];
             int lo[3], hi[3];
@@ -352,18 +406,28 @@ static void contacts(orc_sim* s, double dt) {
                             vrel[a] = (s->Vh[3 * j + a] + wj[a]) - (s->Vh[3 * i + a] + wi[a]);
                         double F[3], ov;
                         orc_pair_force(&s->p, s->R[i], s->R[j], d, vrel, dt, h->ft, F, &ov);
-                        double ti[3], tj[3], Fm[3] = {-F[0], -F[1], -F[2]};
-                        cross(ri, F, ti);
-                        cross(rj, Fm, tj);
-                        for (int a = 0; a < 3; ++a) {
-                            s->Fc[3 * i + a] += F[a];
-                            s->Fc[3 * j + a] -= F[a];
-                            s->Tc[3 * i + a] += ti[a];
-                            s->Tc[3 * j + a] += tj[a];
-                        }
+                        pair_hit* e = pair_push(&s->pairs[i]);
+                        double Fm[3] = {-F[0], -F[1], -F[2]};
+                        e->j = j;
+                        for (int a = 0; a < 3; ++a) e->F[a] = F[a];
+                        cross(ri, F, e->ti);
+                        cross(rj, Fm, e->tj);
                     }
         }
     }
+    memset(s->Fc, 0, sizeof(double) * 3 * np);
+    memset(s->Tc, 0, sizeof(double) * 3 * np);
+    for (int i = 0; i < np; ++i)
+        for (int k = 0; k < s->pairs[i].n; ++k) {
+            const pair_hit* e = &s->pairs[i].e[k];
+            int j = e->j;
+            for (int a = 0; a < 3; ++a) {
+                s->Fc[3 * i + a] += e->F[a];
+                s->Fc[3 * j + a] -= e->F[a];
+                s->Tc[3 * i + a] += e->ti[a];
+                s->Tc[3 * j + a] += e->tj[a];
+            }
+        }
 }
 
 /* Eqs. 9-10 (spheres: I = 2/5 m R^2, no gyroscopic term), velocity Verlet
@@ -430,32 +494,43 @@ static void dem_substeps(orc_sim* s) {
 static void paint(const orc_sim* s, int* owner) {
     int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
     double* best = s->best;
-    for (long n = 0; n < s->N; ++n) owner[n] = -1;
-    for (int p = 0; p < s->np; ++p) {
-        double cx = s->X[3 * p], cy = s->X[3 * p + 1], cz = s->X[3 * p + 2], R = s->R[p];
-        int x0 = (int)ceil(cx - R), x1 = (int)floor(cx + R);
-        int y0 = (int)ceil(cy - R), y1 = (int)floor(cy + R);
-        int z0 = (int)ceil(cz - R), z1 = (int)floor(cz + R);
-        for (int xi = x0; xi <= x1; ++xi) {
-            int x;
+    /* x-planes in parallel; within a plane every sphere image that reaches
+     * it, in sphere order (the smallest ratio wins, ties to the lowest
+     * index, so the order of the images does not matter) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int x = 0; x < nx; ++x) {
+        for (long n = nidx(s, x, 0, 0); n < nidx(s, x, 0, 0) + (long)ny * nz; ++n) owner[n] = -1;
+        if (!s->px && (x == 0 || x == nx - 1)) continue;
+        for (int p = 0; p < s->np; ++p) {
+            double cx = s->X[3 * p], cy = s->X[3 * p + 1], cz = s->X[3 * p + 2], R = s->R[p];
+            int x0 = (int)ceil(cx - R), x1 = (int)floor(cx + R);
+            int y0 = (int)ceil(cy - R), y1 = (int)floor(cy + R);
+            int z0 = (int)ceil(cz - R), z1 = (int)floor(cz + R);
+            /* unwrapped coordinates xi in [x0, x1] that land on plane x */
+            int k0 = 0, k1 = 0;
             if (s->px) {
-                x = wrapi(xi, nx);
-            } else {
-                if (xi <= 0 || xi >= nx - 1) continue;
-                x = xi;
+                k0 = (int)ceil((double)(x0 - x) / nx);
+                k1 = (int)floor((double)(x1 - x) / nx);
+            } else if (x < x0 || x > x1) {
+                continue;
             }
-            for (int yi = y0; yi <= y1; ++yi) {
-                int y = wrapi(yi, ny);
-                for (int zi = z0; zi <= z1; ++zi) {
-                    int z = wrapi(zi, nz);
-                    double dx = xi - cx, dy = yi - cy, dz = zi - cz;
-                    double d2 = dx * dx + dy * dy + dz * dz;
-                    if (d2 < R * R) {
-                        long n = nidx(s, x, y, z);
-                        double ratio = d2 / (R * R);
-                        if (owner[n] < 0 || ratio < best[n] || (ratio == best[n] && p < owner[n])) {
-                            owner[n] = p;
-                            best[n] = ratio;
+            for (int k = k0; k <= k1; ++k) {
+                int xi = x + k * nx;
+                for (int yi = y0; yi <= y1; ++yi) {
+                    int y = wrapi(yi, ny);
+                    for (int zi = z0; zi <= z1; ++zi) {
+                        int z = wrapi(zi, nz);
+                        double dx = xi - cx, dy = yi - cy, dz = zi - cz;
+                        double d2 = dx * dx + dy * dy + dz * dz;
+                        if (d2 < R * R) {
+                            long n = nidx(s, x, y, z);
+                            double ratio = d2 / (R * R);
+                            if (owner[n] < 0 || ratio < best[n] || (ratio == best[n] && p < owner[n])) {
+                                owner[n] = p;
+                                best[n] = ratio;
+                            }
                         }
                     }
                 }
@@ -557,7 +632,10 @@ static void lbm_step(orc_sim* s) {
         s->trace[s->trace_len++] = cnt ? sum / cnt : NAN;
     }
 
-    /* collision, Eq. 4 */
+    /* collision, Eq. 4 (node by node; independent) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (long n = 0; n < N; ++n) {
         if (s->owner[n] >= 0) continue;
         double fm[Q];
@@ -566,51 +644,109 @@ static void lbm_step(orc_sim* s) {
         for (int m = 0; m < Q; ++m) s->f[m * N + n] = fm[m];
     }
 
-    /* streaming, Eq. 5, with half-way bounce-back, Eqs. 14-15 */
-    memset(s->fn, 0, sizeof(double) * Q * N);
-    for (int x = 0; x < nx; ++x)
-        for (int y = 0; y < ny; ++y)
-            for (int z = 0; z < nz; ++z) {
-                long n = nidx(s, x, y, z);
-                if (s->owner[n] >= 0) continue;
-                for (int m = 0; m < Q; ++m) {
-                    double ft = s->f[m * N + n];
-                    int xx = x + CX[m];
-                    if (s->px) {
-                        xx = wrapi(xx, nx);
-                    } else if (xx < 0 || xx >= nx) {
-                        s->fn[OPP[m] * N + n] = ft;
-                        continue;
-                    }
-                    long k = nidx(s, xx, wrapi(y + CY[m], ny), wrapi(z + CZ[m], nz));
-                    int p = s->owner[k];
-                    if (p < 0) {
-                        s->fn[m * N + k] = ft;
-                        continue;
-                    }
-                    double xb = x + 0.5 * CX[m], yb = y + 0.5 * CY[m], zb = z + 0.5 * CZ[m];
-                    double r[3], wr[3], Vb[3];
-                    lever(s, xb, yb, zb, p, r);
-                    cross(&s->W[3 * p], r, wr);
-                    for (int a = 0; a < 3; ++a) Vb[a] = s->V[3 * p + a] + wr[a];
-                    double cv = CX[m] * Vb[0] + CY[m] * Vb[1] + CZ[m] * Vb[2];
-                    /* Eq. 14 with rho_w = rho_f and 2 w / c_s^2 = 6 w */
-                    double back = ft - 6.0 * WT[m] * rf * cv;
-                    s->fn[OPP[m] * N + n] = back;
-                    /* Eq. 15 taken about the rest state: the mean pressure
-                     * rho_f c_s^2 acts on the whole grain (the granular
-                     * stress of Eq. 13 is an effective stress), so the
-                     * exchanged momentum is counted from 2 w rho_f */
-                    double q = ft + back - 2.0 * WT[m] * rf;
-                    double Fl[3] = {CX[m] * q, CY[m] * q, CZ[m] * q};
-                    double t[3];
-                    cross(r, Fl, t);
-                    for (int a = 0; a < 3; ++a) {
-                        s->Fh[3 * p + a] += Fl[a];
-                        s->Th[3 * p + a] += t[a];
+    /* streaming, Eq. 5, with half-way bounce-back, Eqs. 14-15.  Every
+     * target slot has exactly one writer (the upstream node, or the node
+     * itself when the upstream neighbour is solid or outside), so the
+     * x-planes stream in parallel; the link force and torque of each plane
+     * are summed in that plane's list and the lists added in x order. */
+    const int np = s->np;
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
+        double* acc = (double*)calloc(6 * (size_t)(np > 0 ? np : 1), sizeof(double));
+        int* touched = (int*)malloc(sizeof(int) * (size_t)(np > 0 ? np : 1));
+        unsigned char* mark = (unsigned char*)calloc((size_t)(np > 0 ? np : 1), 1);
+        /* the new lattice starts from zero (solid nodes keep zeros); the
+         * implicit barrier of the loop separates this from the streaming */
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int x = 0; x < nx; ++x)
+            for (int m = 0; m < Q; ++m)
+                memset(&s->fn[m * N + nidx(s, x, 0, 0)], 0, sizeof(double) * (size_t)ny * nz);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int x = 0; x < nx; ++x) {
+            int nt = 0;
+            for (int y = 0; y < ny; ++y)
+                for (int z = 0; z < nz; ++z) {
+                    long n = nidx(s, x, y, z);
+                    if (s->owner[n] >= 0) continue;
+                    for (int m = 0; m < Q; ++m) {
+                        double ft = s->f[m * N + n];
+                        int xx = x + CX[m];
+                        if (s->px) {
+                            xx = wrapi(xx, nx);
+                        } else if (xx < 0 || xx >= nx) {
+                            s->fn[OPP[m] * N + n] = ft;
+                            continue;
+                        }
+                        long k = nidx(s, xx, wrapi(y + CY[m], ny), wrapi(z + CZ[m], nz));
+                        int p = s->owner[k];
+                        if (p < 0) {
+                            s->fn[m * N + k] = ft;
+                            continue;
+                        }
+                        double xb = x + 0.5 * CX[m], yb = y + 0.5 * CY[m], zb = z + 0.5 * CZ[m];
+                        double r[3], wr[3], Vb[3];
+                        lever(s, xb, yb, zb, p, r);
+                        cross(&s->W[3 * p], r, wr);
+                        for (int a = 0; a < 3; ++a) Vb[a] = s->V[3 * p + a] + wr[a];
+                        double cv = CX[m] * Vb[0] + CY[m] * Vb[1] + CZ[m] * Vb[2];
+                        /* Eq. 14 with rho_w = rho_f and 2 w / c_s^2 = 6 w */
+                        double back = ft - 6.0 * WT[m] * rf * cv;
+                        s->fn[OPP[m] * N + n] = back;
+                        /* Eq. 15 taken about the rest state: the mean pressure
+                         * rho_f c_s^2 acts on the whole grain (the granular
+                         * stress of Eq. 13 is an effective stress), so the
+                         * exchanged momentum is counted from 2 w rho_f; the
+                         * literal form (link_literal) omits that reference */
+                        double q = ft + back - (s->link_literal ? 0.0 : 2.0 * WT[m] * rf);
+                        double Fl[3] = {CX[m] * q, CY[m] * q, CZ[m] * q};
+                        double t[3];
+                        cross(r, Fl, t);
+                        if (!mark[p]) {
+                            mark[p] = 1;
+                            touched[nt++] = p;
+                        }
+                        for (int a = 0; a < 3; ++a) {
+                            acc[6 * p + a] += Fl[a];
+                            acc[6 * p + 3 + a] += t[a];
+                        }
                     }
                 }
+            plane_list* pl = &s->plane_acc[x];
+            pl->n = 0;
+            if (nt > pl->cap) {
+                pl->cap = nt;
+                pl->e = (plane_sum*)realloc(pl->e, sizeof(plane_sum) * nt);
             }
+            for (int k = 0; k < nt; ++k) {
+                int p = touched[k];
+                plane_sum* e = &pl->e[pl->n++];
+                e->p = p;
+                for (int a = 0; a < 3; ++a) {
+                    e->F[a] = acc[6 * p + a];
+                    e->T[a] = acc[6 * p + 3 + a];
+                }
+                for (int a = 0; a < 6; ++a) acc[6 * p + a] = 0.0;
+                mark[p] = 0;
+            }
+        }
+        free(acc);
+        free(touched);
+        free(mark);
+    }
+    for (int x = 0; x < nx; ++x)
+        for (int k = 0; k < s->plane_acc[x].n; ++k) {
+            const plane_sum* e = &s->plane_acc[x].e[k];
+            for (int a = 0; a < 3; ++a) {
+                s->Fh[3 * e->p + a] += e->F[a];
+                s->Th[3 * e->p + a] += e->T[a];
+            }
+        }
 
     /* inlet and outlet (Section 2.4; Eq. 25 evaluated at the new time) */
     if (!s->px) {
@@ -664,7 +800,8 @@ orc_sim* orc_create(const orc_params* p) {
     s->owner = (int*)malloc(sizeof(int) * s->N);
     s->owner_new = (int*)malloc(sizeof(int) * s->N);
     s->best = (double*)malloc(sizeof(double) * s->N);
-    if (!s->f || !s->fn || !s->owner || !s->owner_new || !s->best) {
+    s->plane_acc = (plane_list*)calloc((size_t)p->nx, sizeof(plane_list));
+    if (!s->f || !s->fn || !s->owner || !s->owner_new || !s->best || !s->plane_acc) {
         orc_destroy(s);
         return NULL;
     }
@@ -703,6 +840,10 @@ int orc_set_packing(orc_sim* s, int n, const double* X, const double* R, const d
         for (int i = 0; i < s->np; ++i) free(s->hist[i].e);
         free(s->hist);
     }
+    if (s->pairs) {
+        for (int i = 0; i < s->np; ++i) free(s->pairs[i].e);
+        free(s->pairs);
+    }
     s->np = n;
     int nn = n > 0 ? n : 1;
     s->X = (double*)calloc(3 * nn, sizeof(double));
@@ -724,6 +865,7 @@ int orc_set_packing(orc_sim* s, int n, const double* X, const double* R, const d
     s->Fa = (double*)calloc(3 * nn, sizeof(double));
     s->Ta = (double*)calloc(3 * nn, sizeof(double));
     s->hist = (hist_list*)calloc(nn, sizeof(hist_list));
+    s->pairs = (pair_list*)calloc(nn, sizeof(pair_list));
     for (int i = 0; i < n; ++i) {
         if (!(R[i] > 0)) return -1;
         for (int a = 0; a < 3; ++a) {
@@ -867,6 +1009,32 @@ void orc_destroy(orc_sim* s) {
         for (int i = 0; i < s->np; ++i) free(s->hist[i].e);
         free(s->hist);
     }
+    if (s->pairs) {
+        for (int i = 0; i < s->np; ++i) free(s->pairs[i].e);
+        free(s->pairs);
+    }
+    if (s->plane_acc) {
+        for (int x = 0; x < s->p.nx; ++x) free(s->plane_acc[x].e);
+        free(s->plane_acc);
+    }
     free(s->trace);
     free(s);
+}
+
+void orc_set_link_form(orc_sim* s, int literal) { s->link_literal = literal ? 1 : 0; }
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

@@ -45,6 +45,13 @@ void orc_contact_forces(const orc_sim* s, double* Fc, double* Tc);
 long long orc_probe(const orc_sim* s, double* trace, long long max_len);
 void orc_destroy(orc_sim* s);
 
+/* 1: count the link momentum as printed in Eq. 15, c_d (f~_d + f_d*);
+ * 0 (default): about the rest state, c_d (f~_d + f_d* - 2 w_d rho_f). */
+void orc_set_link_form(orc_sim* s, int literal);
+/* OpenMP threads of every later call (results do not depend on it). */
+void orc_set_threads(int n);
+int orc_get_threads(void);
+
 /* single-node pieces, exposed for the pins */
 void orc_lattice(int* cx, int* cy, int* cz, double* w, int* opp);
 void orc_equilibrium(double rho, double ux, double uy, double uz, double* feq);

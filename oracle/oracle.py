@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
                 os.path.getmtime(_SRC), os.path.getmtime(_SRC[:-2] + ".h")):
             tmp = _LIB + f".tmp{os.getpid()}"
-            subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE",
+            subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fopenmp",
                                    "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
             os.replace(tmp, _LIB)
     return _LIB
@@ -73,6 +73,9 @@ def _load():
         lib.orc_source_density.restype = d
         lib.orc_source_density.argtypes = [C.c_void_p, ll]
         lib.orc_pair_force.argtypes = [P(_Params), d, d, P(d), P(d), d, P(d), P(d), P(d)]
+        lib.orc_set_link_form.argtypes = [C.c_void_p, i]
+        lib.orc_set_threads.argtypes = [i]
+        lib.orc_get_threads.restype = i
         _lib = lib
     return _lib
 
@@ -88,6 +91,15 @@ def _f64(a, shape=None):
     if shape is not None:
         a = a.reshape(shape)
     return a
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle (its results do not depend on the count)."""
+    _load().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(_load().orc_get_threads())
 
 
 def lattice():
@@ -183,6 +195,11 @@ class Oracle:
 
     def step(self, n=1):
         _load().orc_step(self._s, int(n))
+
+    def set_link_form(self, literal: bool):
+        """True: the link momentum as printed in Eq. 15, c_d (f~_d + f_d*);
+        False (default): about the rest state (the reading both sides use)."""
+        _load().orc_set_link_form(self._s, 1 if literal else 0)
 
     @property
     def t(self):

@@ -302,3 +302,85 @@ def test_moving_spheres_mass_budget(seed):
             checked_links += int(sel.sum())
         assert abs(m1 - pred) < 1e-11 * m0, (m1 - pred, m1 - m0)
     assert checked_links > 1000
+
+
+def _d3q19(golden_dir):
+    """c[19, 3] from the printed columns of Eq. 3 and the weights of Eq. 8."""
+    rows = [list(map(int, l.split())) for l in open(os.path.join(golden_dir, "d3q19_velocities.txt"))
+            if l.strip() and not l.startswith("#")]
+    c = np.array(rows).T
+    c2 = (c * c).sum(1)
+    return c, np.where(c2 == 0, 1 / 3, np.where(c2 == 1, 1 / 18, 1 / 36))
+
+
+def test_link_momentum_rest_state_equals_literal_on_a_wetted_sphere():
+    """Reading of Eq. 15: the link momentum is counted about the rest state,
+    c_d (f~_d + f_d* - 2 w_d rho_f), instead of the printed c_d (f~_d + f_d*).
+    The two differ by 2 rho_f sum_links w_d c_d (and its moment), which is
+    zero over the closed staircase of a sphere whose every neighbour node is
+    fluid: so a moving, spinning sphere alone in a periodic box feels the
+    same force and torque under both forms, step after step (and, since
+    that drives it, follows the same path)."""
+    w = workloads.Workload(name="wet", nx=24, ny=22, nz=21, tau=0.8, inlet=workloads.X_PERIODIC,
+                           X=np.array([[11.3, 10.6, 9.9]]), R=np.array([4.6]),
+                           V=np.array([[0.012, -0.007, 0.004]]), W=np.array([[0.002, 0.0015, -0.003]]),
+                           fixed=np.zeros(1, np.uint8), rho_p=2.0, dem_substeps=2)
+    a, b = oracle.Oracle(w), oracle.Oracle(w)
+    b.set_link_form(True)
+    for _ in range(6):
+        a.step(5)
+        b.step(5)
+        pa, pb = a.particles(), b.particles()
+        assert np.abs(pa["Fh"]).max() > 1e-4          # a real drag, not zero
+        assert np.abs(pa["Fh"] - pb["Fh"]).max() < 1e-12
+        assert np.abs(pa["Th"] - pb["Th"]).max() < 1e-12
+        assert np.abs(pa["X"] - pb["X"]).max() < 1e-13
+    # the staircase moved: nodes were covered and uncovered on the way
+    assert a.t == 30
+
+
+def test_link_momentum_forms_differ_by_the_dry_contact_caps(golden_dir):
+    """On two touching spheres the two readings of Eq. 15 differ, for sphere
+    p, by exactly -2 rho_f sum w_d c_d over the node pairs (s, s - c_d) with
+    s owned by p and s - c_d owned by the other sphere -- the dry contact
+    caps -- and the torque by the moment of those terms about X_p at the
+    link midpoint s - c_d / 2.  The pairs are enumerated here from the owner
+    map and the printed velocity set, independently of the oracle's loops;
+    the spheres are fixed, so both runs share every population."""
+    c, wts = _d3q19(golden_dir)
+    X = np.array([[9.62, 8.41, 7.93], [17.03, 9.26, 9.48]])
+    R = np.array([4.2, 3.9])
+    w = workloads.Workload(name="lens2", nx=27, ny=18, nz=17, tau=0.75, inlet=workloads.X_PERIODIC,
+                           X=X, R=R, fixed=np.ones(2, np.uint8), dem_substeps=1)
+    a, b = oracle.Oracle(w), oracle.Oracle(w)
+    b.set_link_form(True)
+    rng = np.random.default_rng(11)
+    f = a.populations() * (1.0 + rng.uniform(-2e-3, 2e-3, a.populations().shape))
+    a.set_populations(f)
+    b.set_populations(f)
+    own = a.owner()
+    shape = np.array(own.shape)
+    L = shape.astype(float)
+    a.step(3)
+    b.step(3)
+    dF, dT = np.zeros((2, 3)), np.zeros((2, 3))
+    npairs = 0
+    for p, q in ((0, 1), (1, 0)):
+        S = np.argwhere(own == p)
+        for m in range(18):
+            nb = (S - c[m]) % shape
+            sel = own[nb[:, 0], nb[:, 1], nb[:, 2]] == q
+            if not sel.any():
+                continue
+            npairs += int(sel.sum())
+            term = -2.0 * w.rho_f * wts[m] * c[m]
+            mid = S[sel] - 0.5 * c[m] - X[p]
+            mid -= L * np.round(mid / L)
+            dF[p] += sel.sum() * term
+            dT[p] += np.cross(mid, term).sum(0)
+    assert npairs > 10
+    Fa, Fb = a.particles()["Fh"], b.particles()["Fh"]
+    Ta, Tb = a.particles()["Th"], b.particles()["Th"]
+    assert np.abs(dF).max() > 1e-3
+    assert np.abs((Fb - Fa) - dF).max() < 1e-12, (Fb - Fa, dF)
+    assert np.abs((Tb - Ta) - dT).max() < 1e-11, (Tb - Ta, dT)

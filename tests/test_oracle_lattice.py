@@ -125,6 +125,41 @@ def test_source_waveforms():
         assert s.source_density(51) == 1.0
 
 
+def test_ricker_pulse_shape():
+    """The Ricker pulse (the sweep's added waveform, not in Table 2):
+    r(t) = (1 - 2 a^2) exp(-a^2), a = pi f (t - t0), f = omega / 2 pi.  Pinned
+    by what the standard wavelet fixes and the formula alone does not give
+    away: its peak value at t0, zero crossings at a = +-1/sqrt(2), minima of
+    -2 exp(-3/2) at a = +-sqrt(3/2), zero time integral, and an amplitude
+    spectrum f'^2 exp(-f'^2 / f^2) that peaks at the peak frequency f.  A
+    wrong factor in a (2 pi, pi or 1/2 misplaced) moves the crossings and
+    the spectral peak; a wrong sign breaks the peak value."""
+    period, t0, amp = 200.0, 400.0, 2e-3
+    f = 1.0 / period
+    w = workloads.plane_wave()
+    w.waveform, w.amplitude, w.omega, w.t0, w.t_n = workloads.RICKER, amp, 2 * math.pi * f, t0, -1
+    s = oracle.Oracle(w)
+    T = np.arange(0, 4096)
+    r = np.array([s.source_density(int(t)) - 1.0 for t in T]) / amp
+    assert abs(r[int(t0)] - 1.0) < 1e-15 and r.argmax() == int(t0)
+    tz = 1.0 / (math.sqrt(2.0) * math.pi * f)          # zero crossing offset
+    for side in (-1, 1):
+        a, b = int(math.floor(t0 + side * tz)), int(math.ceil(t0 + side * tz))
+        assert r[a] * r[b] < 0, (side, r[a], r[b])
+        tm = t0 + side * math.sqrt(1.5) / (math.pi * f)  # minimum
+        k = int(round(tm))
+        assert abs(r[k] + 2 * math.exp(-1.5)) < 1e-3
+        assert r[k] <= r[k - 1] + 1e-3 and r[k] <= r[k + 1] + 1e-3
+    assert abs(r.sum()) < 1e-9 * period                 # zero integral (smooth, decayed)
+    spec = np.abs(np.fft.rfft(r, 1 << 18))
+    fr = np.fft.rfftfreq(1 << 18)
+    assert abs(fr[spec.argmax()] - f) < 0.01 * f
+    # switched off after t_n like every other source
+    w.t_n = 300
+    s2 = oracle.Oracle(w)
+    assert s2.source_density(301) == 1.0 and s2.source_density(300) != 1.0
+
+
 def test_uniform_flow_is_fixed_point():
     """A uniform equilibrium flow in a fully periodic box never changes."""
     w = workloads.Workload(name="u", nx=6, ny=5, nz=4, tau=0.7, inlet=workloads.X_PERIODIC,
