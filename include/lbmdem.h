@@ -59,8 +59,8 @@ extern "C" {
 
 /* distribution storage (the arithmetic is FP32 in every case) */
 #define LBMDEM_F32 0      /* f_i - w_i rho_f stored as FP32                  */
-#define LBMDEM_BF16_DEV 1 /* f_i - w_i rho_f stored as BF16 (reserved)       */
-#define LBMDEM_F16_DEV 2  /* f_i - w_i rho_f stored as FP16 (reserved)       */
+#define LBMDEM_BF16_DEV 1 /* f_i - w_i rho_f stored as BF16                 */
+#define LBMDEM_F16_DEV 2  /* f_i - w_i rho_f stored as FP16 scaled by 2^12   */
 
 /* x boundaries */
 #define LBMDEM_INLET_PRESSURE 0 /* Section 2.4 pressure inlet at x = 0 with rho(t)   */
@@ -82,7 +82,7 @@ typedef struct {
     int32_t nx, ny, nz;   /* lattice; nx = propagation axis; nx <= 4096, ny, nz <= 1024 */
     double tau;           /* BGK relaxation time, Eq. 4; must exceed 0.5              */
     double rho_f;         /* mean fluid density, Eq. 6                                */
-    int32_t storage;      /* LBMDEM_F32 (16-bit forms reserved)                       */
+    int32_t storage;      /* LBMDEM_F32 | LBMDEM_BF16_DEV | LBMDEM_F16_DEV            */
     int32_t inlet;        /* LBMDEM_INLET_PRESSURE | LBMDEM_X_WALL | LBMDEM_X_PERIODIC */
     int32_t outlet;       /* LBMDEM_OUT_*; ignored when x is periodic                 */
     int32_t dem_substeps; /* K >= 1 velocity-Verlet substeps per LBM step             */
@@ -165,8 +165,9 @@ int lbm_dem_read_particles(lbmdem_ctx* c, double* X, double* V, double* Omega, d
  *  - At most 65536 spheres: a larger packing returns LBMDEM_ERR_CAPACITY
  *    with a message, and nothing is read.
  *  - The first call on a device looks up the array's device address (once
- *    per device, with that device current); make that first call before any
- *    stream capture on the device.
+ *    per device and CUDA context, with that device current; again after the
+ *    device's context was reset or replaced); make that first call before
+ *    any stream capture on the device.
  *  - The array is shared by all calls on a device and keeps the last call's
  *    contents (every value copied out is written by the same call).  Calls
  *    whose GPU work overlaps (two contexts of one device used from two host

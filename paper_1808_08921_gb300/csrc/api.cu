@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <cuda.h>
 #include <string>
 #include <vector>
 
@@ -1650,22 +1651,65 @@ constexpr int NOALLOC_MAX_SPHERES = 65536;  // 19 doubles each: 9.5 MiB
 constexpr int NOALLOC_MAX_DEVICES = 64;
 __device__ __align__(256) double noalloc_particle_scratch[19 * NOALLOC_MAX_SPHERES];
 
+// The array's address belongs to a CUDA context, not to a device ordinal:
+// after cudaDeviceReset (or under another context made current by the
+// caller) the device has a new context and the array a new address.  The
+// cache is therefore keyed on the device and the unique id of the context
+// current at the call (cuCtxGetId, reached through the runtime's driver
+// entry points, so no link against the driver library is needed).
+struct NoallocSlot {
+    unsigned long long ctx_id = 0;
+    double* ptr = nullptr;
+};
 std::mutex noalloc_mutex;
-double* noalloc_scratch_ptr[NOALLOC_MAX_DEVICES] = {};
+NoallocSlot noalloc_slot[NOALLOC_MAX_DEVICES];
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
+PfnCtxGetCurrent noalloc_get_current = nullptr;
+PfnCtxGetId noalloc_get_id = nullptr;
 
-// Device address of the array on device `dev` (which must be current),
-// looked up once per device on the first call.
+// Unique id of the context current on this thread (0 if none); call with
+// noalloc_mutex held.
+cudaError_t noalloc_context_id(unsigned long long* id) {
+    *id = 0;
+    if (!noalloc_get_current || !noalloc_get_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return e;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorSymbolNotFound;
+        noalloc_get_current = (PfnCtxGetCurrent)f1;
+        noalloc_get_id = (PfnCtxGetId)f2;
+    }
+    CUcontext ctx = nullptr;
+    if (noalloc_get_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaSuccess;
+    if (noalloc_get_id(ctx, id) != CUDA_SUCCESS) *id = 0;
+    return cudaSuccess;
+}
+
+// Device address of the array on device `dev` (which must be current):
+// looked up on the first call on the device's current context, and again
+// whenever the context changed since.
 int noalloc_scratch(lbmdem_ctx* c, int dev, double** out) {
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
         return fail(c, LBMDEM_ERR_INVALID_ARG, "read_particles_noalloc: device %d beyond %d", dev,
                     NOALLOC_MAX_DEVICES);
     std::lock_guard<std::mutex> lock(noalloc_mutex);
-    if (!noalloc_scratch_ptr[dev]) {
+    unsigned long long id = 0;
+    CK(noalloc_context_id(&id));
+    NoallocSlot& sl = noalloc_slot[dev];
+    if (!sl.ptr || id == 0 || sl.ctx_id != id) {
         double* p = nullptr;
         CK(cudaGetSymbolAddress((void**)&p, noalloc_particle_scratch));
-        noalloc_scratch_ptr[dev] = p;
+        if (id == 0) CK(noalloc_context_id(&id));  // the lookup created the context
+        sl.ptr = p;
+        sl.ctx_id = id;
     }
-    *out = noalloc_scratch_ptr[dev];
+    *out = sl.ptr;
     return 0;
 }
 }  // namespace

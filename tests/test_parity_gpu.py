@@ -6,8 +6,9 @@ Bars (FP32 arithmetic against FP64):
   * density: |rho_gpu - rho_ref| <= 1e-4 rho_ref, and <= 1e-3 of the largest
     density deviation |rho_ref - rho_f| (the signal is ~1e-3 of rho);
   * velocity: |u_gpu - u_ref| <= 1e-4 max |u_ref|;
-  * sphere centres within 1e-6 lattice units; hydrodynamic force within
-    1e-3 of the largest force component.
+  * sphere centres within 1e-6 lattice units; hydrodynamic force and
+    torque (Eqs. 18-19), velocity and angular velocity within 1e-3 of their
+    largest component; orientation quaternions within 1e-5.
 """
 import math
 
@@ -41,15 +42,17 @@ def compare_fields(g, o, rho_f=1.0, sig_tol=1e-3):
     return drho.max(), du, sig, umax
 
 
-def compare_particles(g, o, xtol=1e-6, ftol=1e-3):
+def compare_particles(g, o, xtol=1e-6, ftol=1e-3, qtol=1e-5):
     pg, po = g.particles(), o.particles()
     if len(po["X"]) == 0:
         return 0.0
     dx = np.abs(pg["X"] - po["X"]).max()
     assert dx <= xtol, dx
-    fmax = np.abs(po["Fh"]).max()
-    if fmax > 0:
-        assert np.abs(pg["Fh"] - po["Fh"]).max() <= ftol * fmax + 1e-12
+    for k in ("Fh", "Th", "V", "W"):
+        ref = np.abs(po[k]).max()
+        err = np.abs(pg[k] - po[k]).max()
+        assert err <= ftol * ref + 1e-12, (k, err, ref)
+    assert np.abs(pg["q"] - po["q"]).max() <= qtol, np.abs(pg["q"] - po["q"]).max()
     return dx
 
 
@@ -181,3 +184,31 @@ def test_forced_relayout_keeps_the_state():
     o.step(9)
     compare_fields(g, o)
     compare_particles(g, o)
+
+
+@pytest.mark.parametrize("workload", ["column", "plane_wave"])
+def test_fp64_monitors_match_oracle_totals(workload):
+    """The FP64 totals the GPU accumulates on monitored steps (the drift
+    monitor: sum rho and sum rho u over the fluid nodes, max |u|, Eq. 7) equal
+    the oracle's sums over its fluid nodes of the same state.  A monitored
+    step sums the state it starts from; with fixed spheres no node converts,
+    so that is the oracle's state after the same number of completed steps."""
+    if workload == "column":
+        w = workloads.config_parity(steps=48)
+        w.fixed = np.ones(len(w.R), np.uint8)
+    else:
+        w = workloads.plane_wave(nx=200, ny=2, nz=3, amplitude=1e-3, omega=0.05, steps=48)
+    g, o = _sim(w, monitor_every=16), oracle.Oracle(w)
+    g.step(48)
+    mon = g.monitors()
+    k = int(mon[5])
+    assert k == 47
+    o.step(k)
+    ro, uo, so = o.fields()
+    fl = so == 0
+    j = (uo * ro[None])[:, fl].sum(axis=1)
+    assert abs(mon[0] - ro[fl].sum()) <= 1e-4 * np.abs(ro[fl] - w.rho_f).sum()
+    jabs = np.abs(uo * ro[None])[:, fl].sum(axis=1)
+    assert np.all(np.abs(mon[1:4] - j) <= 1e-4 * jabs + 1e-15), (mon[1:4], j)
+    umax = np.sqrt((uo ** 2).sum(axis=0))[fl].max()
+    assert abs(mon[4] - umax) <= 1e-4 * umax
