@@ -497,9 +497,9 @@ def run_sweep(args):
     """The source sweep: 48 independent columns 32 x 32 x L (L 256..1024, sine
     and Ricker sources, ceil(L sqrt 3) steps each).  The autotuner picks the
     DEM subcycle and the collide+stream tile on the median column; the
-    columns then run as one batch (one CUDA graph per 16-step chunk) and, for
-    comparison, one after another.  value = fluid-node updates of all columns
-    per second of the batched run."""
+    columns then run as one batch (one launch of one CUDA graph: a device-side
+    loop per column) and, for comparison, one after another.  value =
+    fluid-node updates of all columns per second of the batched run."""
     import torch
 
     import workloads

@@ -229,26 +229,40 @@ int lbm_dem_adjoint(lbmdem_ctx* c, int64_t steps, int32_t every, const double* t
  * The paper's study of the acoustic source (Section 4.4: input waveforms and
  * frequencies of Table 2) runs one column per source; a batch advances many
  * such independent contexts (columns of any length, packing and source)
- * together.  For each
- * chunk of 16 steps one CUDA graph holds every active column's step kernels
- * as parallel branches, launched once on the batch's own stream.  Columns may
- * take different step counts; a column with fewer than 16 steps left
- * finishes alone through lbm_dem_step.  Per-kernel timing is not recorded for
- * steps taken inside the batch graph.  The contexts stay owned by the caller
- * and must outlive the batch; use no context elsewhere while a batch call
- * runs. */
+ * together, each by its own number of steps, in ONE launch of one CUDA
+ * graph: each column is a parallel branch holding a device-side WHILE loop
+ * (conditional graph node) over pairs of coupled steps and, for an odd
+ * count, an IF node with the last step.  A control kernel ends a column's
+ * loop when its steps are done, when its device status latches an error, or
+ * when the batch's time limit (lbm_dem_batch_set_time_limit) has passed on
+ * the GPU clock, which latches LBMDEM_ERR_TIMEOUT for that column.  The host
+ * takes no part between launch and end: re-layout checks of mobile columns
+ * run before the launch only (a sphere that moves beyond its skin inside the
+ * launch latches LBMDEM_ERR_SKIN).  Per-kernel timing is not recorded inside
+ * the batch graph.  The contexts stay owned by the caller and must outlive
+ * the batch; use no context elsewhere while a batch call runs. */
 typedef struct lbmdem_batch lbmdem_batch; /* opaque, library-owned */
 
 /* Group n contexts (distinct, all on one device, each after set_packing).
  * Errors: INVALID_ARG (NULL, duplicates, mixed devices), STATE, CUDA. */
 int lbm_dem_batch_create(lbmdem_ctx* const* cols, int32_t n, lbmdem_batch** out);
 
-/* Advance column i by steps[i] >= 0 coupled steps (asynchronous like
- * lbm_dem_step; re-layout checks of mobile columns read a few bytes back
- * between chunks).  Errors: INVALID_ARG, a column's latched status, CUDA. */
+/* Wall-clock limit of every following lbm_dem_batch_step launch, in seconds
+ * of GPU time from the launch (0 = none, the default).  A column whose loop
+ * is still running when it passes stops between two steps and latches
+ * LBMDEM_ERR_TIMEOUT; the other columns stop the same way.
+ * Errors: INVALID_ARG (negative or not finite). */
+int lbm_dem_batch_set_time_limit(lbmdem_batch* b, double seconds);
+
+/* Advance column i by steps[i] >= 0 coupled steps in one graph launch
+ * (asynchronous like lbm_dem_step; the graph is built for the call, after a
+ * re-layout check and, for a column at an odd step, one single step).
+ * Errors: INVALID_ARG, a column's latched status, CUDA. */
 int lbm_dem_batch_step(lbmdem_batch* b, const int64_t* steps);
 
-/* Wait for the batch and every column; returns the first column status. */
+/* Wait for the batch and every column; returns the first column status
+ * (0, or e.g. LBMDEM_ERR_TIMEOUT); a column whose loop stopped early is left
+ * at the step it reached. */
 int lbm_dem_batch_sync(lbmdem_batch* b);
 
 /* Graph launches issued by lbm_dem_batch_step so far (-1 for NULL). */

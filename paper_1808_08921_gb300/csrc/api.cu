@@ -1061,29 +1061,37 @@ int lbm_dem_step(lbmdem_ctx* c, int64_t n) {
 }  // extern "C"
 
 // A batch advances several independent contexts (columns) of one device
-// together: for each chunk of BATCH_CHUNK steps one CUDA graph holds every
-// active column's kernels as parallel branches (each column's kernels on its
-// own stream, joined on the batch stream), so the small kernels of many
-// columns share the GPU and one graph launch replaces hundreds of kernel
-// launches.  Columns may ask for different step counts; a column leaves the
-// graph when fewer than BATCH_CHUNK of its steps remain and finishes through
-// lbm_dem_step.  Re-layout checks of mobile columns happen between chunks.
+// together, each by its own number of steps, in ONE launch of one CUDA
+// graph: every column is a parallel branch holding a device-side WHILE
+// loop (a conditional graph node) whose body is two coupled steps of that
+// column (an even and an odd one, so the AA parity of the captured kernels
+// never changes) followed by a control kernel; an IF node after the loop
+// takes a trailing single step when the column's count is odd.  The
+// control kernel counts the column's remaining step pairs down and ends the
+// loop when they run out, when the column's device status latched an error
+// (NaN, capacity, skin) or when the batch's time limit has passed on the
+// GPU clock (%globaltimer), in which case it latches LBMDEM_ERR_TIMEOUT: no
+// loop runs unbounded, and nothing waits on another block.  The host takes
+// no part until the whole sweep has run: re-layout checks happen before the
+// launch only, so a sphere that moves farther than the skin inside the
+// launch latches LBMDEM_ERR_SKIN instead.
 struct lbmdem_batch {
     std::vector<lbmdem_ctx*> cols;
     int device = 0;
     cudaStream_t master = nullptr;
-    cudaEvent_t fork = nullptr, done = nullptr;
-    std::vector<cudaEvent_t> join, pre;
+    cudaEvent_t done = nullptr;
+    std::vector<cudaEvent_t> pre;
     cudaGraphExec_t gexec = nullptr;
-    std::vector<int> gcols;           // columns in the captured graph
-    std::vector<int64_t> glaunch;     // kernels per column in one graph launch
-    int64_t graph_launches = 0;       // graph launches so far
+    DBuf<long long> remaining;         // [n] step pairs left per column (device)
+    DBuf<long long> pairs_dev;         // [n] pair counts the start node reads
+    DBuf<unsigned long long> start_ns; // GPU clock at the launch (device)
+    double time_limit_s = 0.0;         // 0: no limit
+    int64_t graph_launches = 0;        // graph launches so far
+    std::vector<int64_t> requested;    // steps asked of each column by the last launch
     std::string err;
 };
 
 namespace {
-constexpr int BATCH_CHUNK = 16;
-
 int bfail(lbmdem_batch* b, int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -1102,38 +1110,160 @@ int bfail(lbmdem_batch* b, int code, const char* fmt, ...) {
                          __FILE__, __LINE__);                                                      \
     } while (0)
 
+__device__ __forceinline__ unsigned long long gpu_clock_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+struct BatchCtl {
+    long long* remaining;
+    unsigned long long* start_ns;
+    unsigned long long limit_ns;  // 0: none
+};
+
+// at the launch: the GPU clock and every column's pair count
+__global__ void k_batch_start(BatchCtl ctl, const long long* pairs, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *ctl.start_ns = gpu_clock_ns();
+    if (i < n) ctl.remaining[i] = pairs[i];
+}
+
+// end of one loop iteration (two steps) of column i: continue while pairs
+// are left, the column's status is clear and the time limit has not passed
+__global__ void k_batch_loop(BatchCtl ctl, int i, uint32_t* status, cudaGraphConditionalHandle h) {
+    if (threadIdx.x || blockIdx.x) return;
+    const long long r = ctl.remaining[i] - 1;
+    ctl.remaining[i] = r;
+    unsigned go = r > 0 && *status == 0u;
+    if (go && ctl.limit_ns && gpu_clock_ns() - *ctl.start_ns > ctl.limit_ns) {
+        atomicOr(status, ST_TIMEOUT);
+        go = 0;
+    }
+    cudaGraphSetConditional(h, go);
+}
+
+// after the loop of a column with an odd step count: the trailing step runs
+// only if the loop ran to its end with a clear status and time remains
+__global__ void k_batch_tail(BatchCtl ctl, int i, uint32_t* status, cudaGraphConditionalHandle h) {
+    if (threadIdx.x || blockIdx.x) return;
+    unsigned go = ctl.remaining[i] <= 0 && *status == 0u;
+    if (go && ctl.limit_ns && gpu_clock_ns() - *ctl.start_ns > ctl.limit_ns) {
+        atomicOr(status, ST_TIMEOUT);
+        go = 0;
+    }
+    cudaGraphSetConditional(h, go);
+}
+
 void batch_destroy_graph(lbmdem_batch* b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
-    b->gcols.clear();
 }
 
-int batch_capture(lbmdem_batch* b, const std::vector<int>& act) {
+// a conditional node (WHILE or IF) on `graph` after `dep`; its body graph
+// is returned in *body
+int add_conditional(lbmdem_batch* b, cudaGraph_t graph, cudaGraphNode_t dep, cudaGraphConditionalNodeType type,
+                    cudaGraphConditionalHandle h, cudaGraphNode_t* node, cudaGraph_t* body) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = type;
+    cp.conditional.size = 1;
+    BCK(cudaGraphAddNode(node, graph, &dep, nullptr, 1, &cp));
+    *body = cp.conditional.phGraph_out[0];
+    return 0;
+}
+
+// capture `nsteps` coupled steps of column c (parities 0, 1, ...) and then
+// the control kernel `ctl_kernel` into `body`
+int capture_body(lbmdem_batch* b, lbmdem_ctx* c, cudaGraph_t body, int nsteps, void (*ctl_kernel)(BatchCtl, int, uint32_t*, cudaGraphConditionalHandle),
+                 const BatchCtl& ctl, int i, cudaGraphConditionalHandle h) {
+    BCK(cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const bool mon = c->p.monitor_every > 0;
+    for (int k = 0; k < nsteps; ++k) enqueue_step(c, k & 1, mon && k == nsteps - 1);
+    if (ctl_kernel) ctl_kernel<<<1, 32, 0, c->stream>>>(ctl, i, &c->st.p->status, h);
+    cudaGraph_t g = body;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return bfail(b, LBMDEM_ERR_CUDA, "batch body capture: %s", cudaGetErrorString(e));
+    return 0;
+}
+
+// One graph for the whole run: per column a WHILE loop over step pairs and,
+// for an odd count, an IF node with the last step.
+int batch_build(lbmdem_batch* b, const std::vector<int64_t>& steps) {
     batch_destroy_graph(b);
-    BCK(cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal));
-    cudaEventRecord(b->fork, b->master);
-    b->glaunch.assign(b->cols.size(), 0);
-    for (int i : act) {
+    const int n = (int)b->cols.size();
+    std::vector<long long> pairs(n);
+    for (int i = 0; i < n; ++i) pairs[i] = steps[i] / 2;
+    DBuf<long long> dpairs;
+    BCK(dpairs.alloc(n));
+    BCK(cudaMemcpy(dpairs.p, pairs.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
+    BatchCtl ctl{b->remaining.p, b->start_ns.p,
+                 b->time_limit_s > 0 ? (unsigned long long)(b->time_limit_s * 1e9) + 1ull : 0ull};
+    cudaGraph_t root = nullptr;
+    BCK(cudaGraphCreate(&root, 0));
+    auto bail = [&](int r) {
+        cudaGraphDestroy(root);
+        return r;
+    };
+    // the start node: a kernel node reading the pair counts (kept alive by
+    // the graph's copy of the parameters; the buffer is re-made per build)
+    cudaKernelNodeParams kp = {};
+    void* args[3];
+    long long* pp = dpairs.p;
+    args[0] = &ctl;
+    args[1] = &pp;
+    args[2] = (void*)&n;
+    kp.func = (void*)k_batch_start;
+    kp.gridDim = dim3((unsigned)((n + 127) / 128), 1, 1);
+    kp.blockDim = dim3(128, 1, 1);
+    kp.kernelParams = args;
+    cudaGraphNode_t start = nullptr;
+    if (cudaGraphAddKernelNode(&start, root, nullptr, 0, &kp) != cudaSuccess)
+        return bail(bfail(b, LBMDEM_ERR_CUDA, "batch: start node"));
+    for (int i = 0; i < n; ++i) {
         lbmdem_ctx* c = b->cols[i];
-        cudaStreamWaitEvent(c->stream, b->fork, 0);
-        bool tm = c->timing;
+        if (steps[i] <= 0) continue;
+        const bool tm = c->timing;
         c->timing = false;  // per-kernel timing is not recorded inside a batch
-        int64_t l0 = c->launches;
-        bool mon = c->p.monitor_every > 0;
-        for (int k = 0; k < BATCH_CHUNK; ++k) enqueue_step(c, k & 1, mon && k == BATCH_CHUNK - 1);
-        b->glaunch[i] = c->launches - l0;
-        c->launches = l0;
+        const int64_t l0 = c->launches;
+        cudaGraphNode_t last = start;
+        if (pairs[i] > 0) {
+            cudaGraphConditionalHandle h;
+            if (cudaGraphConditionalHandleCreate(&h, root, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+                return bail(bfail(b, LBMDEM_ERR_CUDA, "batch: loop handle"));
+            cudaGraph_t body;
+            if (int r = add_conditional(b, root, start, cudaGraphCondTypeWhile, h, &last, &body)) return bail(r);
+            if (int r = capture_body(b, c, body, 2, k_batch_loop, ctl, i, h)) return bail(r);
+        }
+        if (steps[i] % 2) {
+            cudaGraphConditionalHandle h;
+            if (cudaGraphConditionalHandleCreate(&h, root, 0u, cudaGraphCondAssignDefault) != cudaSuccess)
+                return bail(bfail(b, LBMDEM_ERR_CUDA, "batch: tail handle"));
+            // the decision kernel, then the IF node with one even step
+            cudaKernelNodeParams tp = {};
+            int ii = i;
+            uint32_t* st = &c->st.p->status;
+            void* targs[4] = {&ctl, &ii, &st, &h};
+            tp.func = (void*)k_batch_tail;
+            tp.gridDim = dim3(1, 1, 1);
+            tp.blockDim = dim3(32, 1, 1);
+            tp.kernelParams = targs;
+            cudaGraphNode_t dec = nullptr;
+            if (cudaGraphAddKernelNode(&dec, root, &last, 1, &tp) != cudaSuccess)
+                return bail(bfail(b, LBMDEM_ERR_CUDA, "batch: tail decision node"));
+            cudaGraph_t body;
+            if (int r = add_conditional(b, root, dec, cudaGraphCondTypeIf, h, &last, &body)) return bail(r);
+            if (int r = capture_body(b, c, body, 1, nullptr, ctl, i, h)) return bail(r);
+        }
+        c->launches = l0;  // counted per step when the graph runs
         c->timing = tm;
-        cudaEventRecord(b->join[i], c->stream);
-        cudaStreamWaitEvent(b->master, b->join[i], 0);
     }
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(b->master, &g);
-    if (e != cudaSuccess) return bfail(b, LBMDEM_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&b->gexec, g, 0);
-    cudaGraphDestroy(g);
+    cudaError_t e = cudaGraphInstantiate(&b->gexec, root, 0);
+    cudaGraphDestroy(root);
     if (e != cudaSuccess) return bfail(b, LBMDEM_ERR_CUDA, "batch instantiate: %s", cudaGetErrorString(e));
-    b->gcols = act;
+    // the pair counts are read by the start node at every launch: keep them
+    dpairs.swap(b->pairs_dev);
     return 0;
 }
 }  // namespace
@@ -1157,20 +1287,25 @@ int lbm_dem_batch_create(lbmdem_ctx* const* cols, int32_t n, lbmdem_batch** out)
     b->cols.assign(cols, cols + n);
     b->device = dev;
     if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&b->master, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess ||
+        b->remaining.alloc(n) != cudaSuccess || b->start_ns.alloc(1) != cudaSuccess) {
         lbm_dem_batch_destroy(b);
         return LBMDEM_ERR_CUDA;
     }
-    b->join.resize(n, nullptr);
     b->pre.resize(n, nullptr);
     for (int i = 0; i < n; ++i)
-        if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->pre[i], cudaEventDisableTiming) != cudaSuccess) {
+        if (cudaEventCreateWithFlags(&b->pre[i], cudaEventDisableTiming) != cudaSuccess) {
             lbm_dem_batch_destroy(b);
             return LBMDEM_ERR_CUDA;
         }
     *out = b;
+    return 0;
+}
+
+int lbm_dem_batch_set_time_limit(lbmdem_batch* b, double seconds) {
+    if (!b || !(seconds >= 0) || !std::isfinite(seconds)) return LBMDEM_ERR_INVALID_ARG;
+    b->time_limit_s = seconds;
+    batch_destroy_graph(b);
     return 0;
 }
 
@@ -1185,49 +1320,38 @@ int lbm_dem_batch_step(lbmdem_batch* b, const int64_t* steps) {
         if (c->status_latched)
             return bfail(b, c->status_latched, "column %d: %s", i, status_text(c->status_latched));
         if (int r = ensure_probe(c, c->t + rem[i] + 1)) return bfail(b, r, "column %d: %s", i, c->err.c_str());
-    }
-    for (;;) {
-        // host-side work of each column between graph launches: re-layout
-        // checks, and single steps to reach an even step count
-        std::vector<int> act;
-        for (int i = 0; i < n; ++i) {
-            lbmdem_ctx* c = b->cols[i];
-            if (rem[i] <= 0) continue;
-            if (c->any_mobile && c->steps_until_check <= 0) {
-                bool did;
-                if (int r = check_and_relayout(c, did)) return bfail(b, r, "column %d: %s", i, c->err.c_str());
-            }
-            if (c->t % 2) {
-                if (int r = lbm_dem_step(c, 1)) return bfail(b, r, "column %d: %s", i, c->err.c_str());
-                rem[i] -= 1;
-            }
-            int64_t room = c->any_mobile ? c->steps_until_check : rem[i];
-            if (rem[i] >= BATCH_CHUNK && room >= BATCH_CHUNK && c->t % 2 == 0) act.push_back(i);
+        if (rem[i] == 0) continue;
+        // host-side work before the launch: the re-layout decision, and a
+        // single step to reach an even step count (the loops start even)
+        if (c->any_mobile) {
+            bool did;
+            if (int r = check_and_relayout(c, did)) return bfail(b, r, "column %d: %s", i, c->err.c_str());
         }
-        if (act.empty()) break;
-        if (act != b->gcols || !b->gexec) {
-            if (int r = batch_capture(b, act)) return r;
-        }
-        for (int i : act) {  // the graph runs after each column's earlier work
-            BCK(cudaEventRecord(b->pre[i], b->cols[i]->stream));
-            BCK(cudaStreamWaitEvent(b->master, b->pre[i], 0));
-        }
-        BCK(cudaGraphLaunch(b->gexec, b->master));
-        b->graph_launches += 1;
-        BCK(cudaEventRecord(b->done, b->master));
-        for (int i : act) {  // and before each column's later work
-            lbmdem_ctx* c = b->cols[i];
-            BCK(cudaStreamWaitEvent(c->stream, b->done, 0));
-            c->launches += b->glaunch[i];
-            if (c->p.monitor_every > 0) c->mon_step = c->t + BATCH_CHUNK - 1;
-            c->t += BATCH_CHUNK;
-            c->steps_until_check -= BATCH_CHUNK;
-            rem[i] -= BATCH_CHUNK;
+        if (c->t % 2) {
+            if (int r = lbm_dem_step(c, 1)) return bfail(b, r, "column %d: %s", i, c->err.c_str());
+            rem[i] -= 1;
         }
     }
-    for (int i = 0; i < n; ++i) {  // what is left: fewer than a chunk per column
+    // the graph holds the columns' device pointers and source parameters,
+    // which set_packing, re-layouts and source changes replace: built anew
+    // for every call (instantiation takes milliseconds, a sweep seconds)
+    if (int r = batch_build(b, rem)) return r;
+    b->requested = rem;
+    for (int i = 0; i < n; ++i) {  // the graph runs after each column's earlier work
+        BCK(cudaEventRecord(b->pre[i], b->cols[i]->stream));
+        BCK(cudaStreamWaitEvent(b->master, b->pre[i], 0));
+    }
+    BCK(cudaGraphLaunch(b->gexec, b->master));
+    b->graph_launches += 1;
+    BCK(cudaEventRecord(b->done, b->master));
+    for (int i = 0; i < n; ++i) {  // and before each column's later work
+        lbmdem_ctx* c = b->cols[i];
+        BCK(cudaStreamWaitEvent(c->stream, b->done, 0));
         if (rem[i] <= 0) continue;
-        if (int r = lbm_dem_step(b->cols[i], rem[i])) return bfail(b, r, "column %d: %s", i, b->cols[i]->err.c_str());
+        c->launches += kernels_per_step(c) * rem[i] + (rem[i] + 1) / 2;  // steps + loop control
+        if (c->p.monitor_every > 0) c->mon_step = c->t + rem[i] - 1;
+        c->t += rem[i];  // corrected from the device count by lbm_dem_batch_sync if a loop stopped early
+        c->steps_until_check = 0;
     }
     return 0;
 }
@@ -1236,11 +1360,18 @@ int lbm_dem_batch_sync(lbmdem_batch* b) {
     if (!b) return LBMDEM_ERR_INVALID_ARG;
     BCK(cudaSetDevice(b->device));
     BCK(cudaStreamSynchronize(b->master));
+    int first = 0;
     for (lbmdem_ctx* c : b->cols) {
         int r = lbm_dem_status(c);
-        if (r) return bfail(b, r, "%s", c->err.c_str());
+        // the device counts every step begun: a loop that stopped early
+        // (latched status, time limit) leaves the context at that count
+        if (r && c->lbm) c->t = (int64_t)c->st_host->t;
+        if (r && !first) {
+            first = r;
+            bfail(b, r, "%s", c->err.empty() ? status_text(r) : c->err.c_str());
+        }
     }
-    return 0;
+    return first;
 }
 
 int64_t lbm_dem_batch_graph_launches(const lbmdem_batch* b) { return b ? b->graph_launches : -1; }
@@ -1252,11 +1383,8 @@ void lbm_dem_batch_destroy(lbmdem_batch* b) {
     cudaSetDevice(b->device);
     if (b->master) cudaStreamSynchronize(b->master);
     batch_destroy_graph(b);
-    for (cudaEvent_t e : b->join)
-        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : b->pre)
         if (e) cudaEventDestroy(e);
-    if (b->fork) cudaEventDestroy(b->fork);
     if (b->done) cudaEventDestroy(b->done);
     if (b->master) cudaStreamDestroy(b->master);
     delete b;

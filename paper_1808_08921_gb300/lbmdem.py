@@ -29,7 +29,7 @@ SYMBOLS = ("lbm_dem_default_params", "lbm_dem_init", "lbm_dem_set_packing",
            "lbm_dem_read_probe",
            "lbm_dem_read_monitors", "lbm_dem_read_counters", "lbm_dem_set_timing",
            "lbm_dem_read_timing", "lbm_dem_last_error", "lbm_dem_destroy",
-           "lbm_dem_batch_create", "lbm_dem_batch_step", "lbm_dem_batch_sync",
+           "lbm_dem_batch_create", "lbm_dem_batch_set_time_limit", "lbm_dem_batch_step", "lbm_dem_batch_sync",
            "lbm_dem_batch_graph_launches", "lbm_dem_batch_last_error", "lbm_dem_batch_destroy",
            "lbm_dem_adjoint", "lbm_dem_read_plane_means")
 
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
     lib.lbm_dem_adjoint.argtypes = [vp, i64, i32, P(d), P(d), P(d), P(d), P(d)]
     lib.lbm_dem_read_plane_means.argtypes = [vp, P(d), P(d)]
     lib.lbm_dem_batch_create.argtypes = [P(vp), i32, P(vp)]
+    lib.lbm_dem_batch_set_time_limit.argtypes = [vp, d]
     lib.lbm_dem_batch_step.argtypes = [vp, P(i64)]
     lib.lbm_dem_batch_sync.argtypes = [vp]
     lib.lbm_dem_batch_graph_launches.argtypes = [vp]
@@ -273,8 +274,8 @@ class Sim:
 
 
 class Batch:
-    """Several Sim columns advanced together (lbm_dem_batch_*): one CUDA graph
-    per 16-step chunk holds every active column's kernels."""
+    """Several Sim columns advanced together (lbm_dem_batch_*): one launch of
+    one CUDA graph runs every column's steps (a device-side loop per column)."""
 
     def __init__(self, sims):
         self.sims = list(sims)
@@ -298,6 +299,10 @@ class Batch:
         arr = np.ascontiguousarray(steps, np.int64)
         assert arr.shape == (len(self.sims),)
         self._check(load().lbm_dem_batch_step(self._h, arr.ctypes.data_as(C.POINTER(C.c_int64))))
+
+    def set_time_limit(self, seconds):
+        """GPU-clock limit of each following step() launch (0 = none)."""
+        self._check(load().lbm_dem_batch_set_time_limit(self._h, float(seconds)))
 
     def sync(self):
         self._check(load().lbm_dem_batch_sync(self._h))

@@ -1,7 +1,9 @@
 """Batched columns (lbm_dem_batch_*) through the C ABI: several independent
-columns of different lengths, sources and step counts advanced together give
-the same state as each column advanced alone, and one batched column stays in
-parity with the FP64 oracle."""
+columns of different lengths, sources and step counts advanced together, in
+one graph launch per call, give the same state as each column advanced
+alone; one batched column stays in parity with the FP64 oracle; the batch's
+time limit stops the device loops with LBMDEM_ERR_TIMEOUT (no fault, other
+contexts unaffected)."""
 import numpy as np
 import pytest
 
@@ -36,7 +38,7 @@ def test_batch_matches_columns_run_alone():
     b.step(steps[:2] + [0])
     b.step([0, 0, steps[2]])
     b.sync()
-    assert b.graph_launches >= 3
+    assert b.graph_launches == 2  # one launch per call, whatever the counts
     for s, g, n in zip(alone, cols, steps):
         r0, u0, s0 = s.fields()
         r1, u1, s1 = g.fields()
@@ -79,4 +81,53 @@ def test_batch_rejects_bad_arguments():
     b = lbmdem.Batch([s])
     with pytest.raises(lbmdem.LbmDemError):
         b.step([-1])
+    b.close()
+
+
+def test_one_launch_runs_uneven_columns_to_completion():
+    """Odd and even counts, one of them zero, all in a single graph launch."""
+    ws = _columns()
+    steps = [41, 0, 64]
+    cols = [lbmdem.Sim.from_workload(w) for w in ws]
+    alone = [lbmdem.Sim.from_workload(w) for w in ws]
+    b = lbmdem.Batch(cols)
+    b.step(steps)
+    b.sync()
+    assert b.graph_launches == 1
+    for g, s, n in zip(cols, alone, steps):
+        s.step(n)
+        assert g.counters()["t"] == n
+        assert np.abs(g.particles()["X"] - s.particles()["X"]).max() <= 1e-9
+        r0, _, s0 = s.fields()
+        r1, _, s1 = g.fields()
+        assert np.array_equal(s0, s1) and np.abs(r1 - r0)[s0 == 0].max() <= 1e-9
+    b.close()
+
+
+def test_time_limit_stops_the_loops_with_timeout():
+    """A limit far shorter than the run: every column's device loop stops
+    between steps and latches LBMDEM_ERR_TIMEOUT; the columns stay readable at
+    the step they reached, and a context outside the batch is unaffected."""
+    ws = _columns()
+    cols = [lbmdem.Sim.from_workload(w) for w in ws]
+    b = lbmdem.Batch(cols)
+    b.set_time_limit(1e-6)
+    b.step([400, 400, 400])
+    with pytest.raises(lbmdem.LbmDemError) as ei:
+        b.sync()
+    assert ei.value.code == -5  # LBMDEM_ERR_TIMEOUT
+    import ctypes as C
+    for g in cols:
+        assert g.status() == -5
+        t = g.counters()["t"]
+        assert 2 <= t < 400 and t % 2 == 0
+        # the state stays readable; the read reports the latched status
+        r, u = np.zeros(g.N), np.zeros(3 * g.N)
+        rc = lbmdem.load().lbm_dem_read_fields(g._h, r.ctypes.data_as(C.POINTER(C.c_double)),
+                                               u.ctypes.data_as(C.POINTER(C.c_double)), None)
+        assert rc == -5
+        assert np.isfinite(r).all() and np.isfinite(u).all() and r.max() > 0.9
+    other = lbmdem.Sim.from_workload(ws[0])
+    other.step(20)
+    assert other.status() == 0
     b.close()
