@@ -595,6 +595,48 @@ def adjoint_record(steps, stream_handle=None, every=100):
     h, ha = 1e-3 * tau, 1e-2 * amp
     fd_tau = (forward_loss(tau + h, amp)[0] - forward_loss(tau - h, amp)[0]) / (2 * h)
     fd_amp = (forward_loss(tau, amp + ha)[0] - forward_loss(tau, amp - ha)[0]) / (2 * ha)
+    # sphere positions, through the smooth coupling surrogate (outside the
+    # paper): its adjoint against its forward run, and dL/dX of the six
+    # coordinates of the two spheres nearest the probe against central
+    # differences of the surrogate's own loss
+    # target: the surrogate's trace at (1.03 tau, 1.2 rho') with seeded noise,
+    # so that the residual (and dL/dX) is well above FP32 resolution
+    s = sim(1.03 * tau, 1.2 * amp)
+    _, ptrace = s.surrogate_loss(steps, np.zeros(steps))
+    s.close()
+    ptarget = ptrace + np.random.default_rng(8).normal(0.0, 1e-5 / 3.0, steps)
+    s = sim(tau, amp)
+    s.status()
+    t0 = time.perf_counter()
+    Lp, _ = s.surrogate_loss(steps, ptarget)
+    s.status()
+    t_pf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Lp2, dp_tau, dp_amp, dX, _ = s.adjoint_psm(steps, every, ptarget)
+    t_pa = time.perf_counter() - t0
+    near = np.argsort(np.abs(w.X[:, 0] - w.probe_x))[:2]
+    hx = 5e-3
+    fd_x, ad_x = [], []
+    for p in near:
+        for a in range(3):
+            Xp, Xm = w.X.copy(), w.X.copy()
+            Xp[p, a] += hx
+            Xm[p, a] -= hx
+            s.set_packing(Xp, w.R, None, None, w.fixed)
+            lp, _ = s.surrogate_loss(steps, ptarget)
+            s.set_packing(Xm, w.R, None, None, w.fixed)
+            lm, _ = s.surrogate_loss(steps, ptarget)
+            fd_x.append((lp - lm) / (2 * hx))
+            ad_x.append(float(dX[p, a]))
+    s.close()
+    fd_x, ad_x = np.array(fd_x), np.array(ad_x)
+    positions = {"model": "smooth partially-saturated coupling surrogate (outside the paper; lbm_dem_adjoint_psm)",
+                 "spheres": len(w.R), "cost_ratio": round(t_pa / t_pf, 3), "forward_s": round(t_pf, 4),
+                 "adjoint_s": round(t_pa, 4), "loss": Lp2, "dL_dtau": dp_tau, "dL_damp": dp_amp,
+                 "checked": [[int(p), a] for p in near for a in range(3)],
+                 "dL_dX_checked": ad_x.tolist(), "fd_dL_dX_checked": fd_x.tolist(),
+                 "rel_err_x": float(np.abs(ad_x - fd_x).max() / max(np.abs(fd_x).max(), 1e-300)),
+                 "fd_step_lu": hx}
     return {"metric": "adjoint cost / forward cost", "value": round(t_adj / t_fwd, 3), "unit": "ratio",
             "higher_is_better": False,
             "config": {"workload": w.name, "lattice": [w.nx, w.ny, w.nz], "spheres": len(w.R), "steps": steps,
@@ -602,6 +644,7 @@ def adjoint_record(steps, stream_handle=None, every=100):
             "forward_s": round(t_fwd, 4), "adjoint_s": round(t_adj, 4), "loss": L, "loss_forward": L0,
             "dL_dtau": d_tau, "fd_dL_dtau": fd_tau, "rel_err_tau": abs(d_tau - fd_tau) / max(abs(fd_tau), 1e-300),
             "dL_damp": d_amp, "fd_dL_damp": fd_amp, "rel_err_amp": abs(d_amp - fd_amp) / max(abs(fd_amp), 1e-300),
+            "positions": positions,
             "timing": "wall clock around a device synchronise on both sides (forward: the steps alone; "
                       "adjoint: forward sweep with checkpoints, recomputation and the reverse sweep)"}
 

@@ -225,6 +225,30 @@ int lbm_dem_read_timing(lbmdem_ctx* c, double ms[5], int64_t launches[5]);
 int lbm_dem_adjoint(lbmdem_ctx* c, int64_t steps, int32_t every, const double* target, double* loss,
                     double* dL_dtau, double* dL_damp, double* trace_out);
 
+/* The same misfit's gradient under a smooth surrogate of the coupling, with
+ * respect to the sphere centres as well (not in the paper: with the binary
+ * solid map of Eqs. 14-15 the misfit is piecewise constant in the centres,
+ * so this entry point differentiates a surrogate from the family Section 1
+ * names as the alternative, Noble and Torczynski's collision weighted by
+ * the solid fraction of each cell).  Model: every node carries populations;
+ * solid fraction eps = 1 - prod_p (1 - S(R_p - |x - X_p| + 1/2)), S the cubic
+ * smoothstep (x ends fluid); collision g*_i = g_i - (1 - B)/tau (g_i - g^eq_i)
+ * + B (g_opp(i) - g_i + w_i drho - g^eq_opp(i)), B = eps (tau - 1/2) /
+ * ((1 - eps) + (tau - 1/2)); streaming, inlet and outlet as in the coupled
+ * step; probe p(k) = c_s^2 times the mean density over every node of plane
+ * probe_x.  The surrogate runs from rest at rho_f with the source at time 0
+ * for `steps` steps on its own dense lattice (the context's state is left
+ * unchanged), checkpointed every `every` (>= 1) steps: L = sum_k (p(k) -
+ * target[k])^2, dL/dtau, dL/drho' and dL_dX[n][3] (NULL skips), trace_out
+ * [steps] = p(k) (NULL skips); with all three gradient pointers NULL only
+ * the forward run and the loss are computed.  Device memory, released on
+ * return: (steps/every + every + 6) 19 N FP32 values plus N FP64,
+ * N = nx ny nz (4 19 N FP32 for the forward alone).
+ * Errors: INVALID_ARG, STATE (mobile spheres, no probe, resting-wall inlet),
+ * OOM, CUDA. */
+int lbm_dem_adjoint_psm(lbmdem_ctx* c, int64_t steps, int32_t every, const double* target, double* loss,
+                        double* dL_dtau, double* dL_damp, double* dL_dX, double* trace_out);
+
 /* ---- Batched columns ------------------------------------------------------
  * The paper's study of the acoustic source (Section 4.4: input waveforms and
  * frequencies of Table 2) runs one column per source; a batch advances many

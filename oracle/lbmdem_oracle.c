@@ -59,6 +59,13 @@
  * against it (the two differ only by 2 w_d rho_f c_d summed over the links,
  * which vanishes over the closed staircase of a fully wetted sphere).
  *
+ * orc_set_coupling(s, 1) replaces the momentum-exchange coupling by a
+ * smooth surrogate for gradients in the sphere positions (outside the
+ * paper's chosen method; the paper names the Noble-Torczynski
+ * partially-saturated scheme as the alternative family, Section 1): every
+ * node carries populations and collides with a solid-fraction-weighted
+ * operator (psm_step below), the spheres stay fixed.
+ *
  * Parity pins (tests/test_oracle_*.py): equilibrium moments, BGK
  * conservation, exact streaming shifts, Zou-He moment identities, mass
  * conservation with static spheres in a closed box, y/z momentum balance
@@ -156,6 +163,9 @@ struct orc_sim {
     long long trace_len, trace_cap;
     int have_packing;
     int link_literal;       /* 1: link momentum c_d (f~_d + f_d*) as printed in Eq. 15 */
+    int psm;                /* 1: the smooth partially-saturated surrogate (orc_set_coupling) */
+    double* eps;            /* its solid fraction per node, if given (orc_psm_set_fraction) */
+    double* eps_auto;       /* else from the (fixed) spheres, computed once per packing */
     plane_list* plane_acc;  /* [nx] link sums of each x-plane */
     pair_list* pairs;       /* [np] contacts found from each lower-index sphere */
 };
@@ -786,6 +796,145 @@ static void lbm_step(orc_sim* s) {
     s->fn = tmp;
 }
 
+/* ------------------------------------------------------------ surrogate */
+
+/* Smooth solid fraction of a node (a C1 stand-in for the binary solid map,
+ * the surrogate's only dependence on the sphere centres): sphere p covers
+ * eps_p = S(R_p - |x - X_p| + 1/2) of the node, S the cubic smoothstep
+ * (0 below 0, 3 s^2 - 2 s^3 on [0, 1], 1 above), the distance taken to the
+ * nearest periodic image; overlapping spheres combine as
+ * eps = 1 - prod_p (1 - eps_p).  The x planes 0 and nx-1 stay fluid when x
+ * is not periodic (as in the solid map). */
+static double smoothstep(double v) {
+    if (v <= 0.0) return 0.0;
+    if (v >= 1.0) return 1.0;
+    return v * v * (3.0 - 2.0 * v);
+}
+
+static double psm_fraction_at(const orc_sim* s, int x, int y, int z) {
+    if (!s->px && (x == 0 || x == s->p.nx - 1)) return 0.0;
+    double keep = 1.0;
+    for (int p = 0; p < s->np; ++p) {
+        double r[3];
+        lever(s, x, y, z, p, r);
+        double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        keep *= 1.0 - smoothstep(s->R[p] - d + 0.5);
+    }
+    return 1.0 - keep;
+}
+
+void orc_psm_fraction(const orc_sim* s, double* eps) {
+    for (int x = 0; x < s->p.nx; ++x)
+        for (int y = 0; y < s->p.ny; ++y)
+            for (int z = 0; z < s->p.nz; ++z)
+                eps[nidx(s, x, y, z)] = s->eps ? s->eps[nidx(s, x, y, z)] : psm_fraction_at(s, x, y, z);
+}
+
+/* One step of the surrogate, in the order of lbm_step: at every node the
+ * Noble-Torczynski collision with solid fraction eps and a resting solid,
+ *   f*_i = f_i - (1 - B)/tau (f_i - f^eq_i) + B Om_i,
+ *   B = eps (tau - 1/2) / ((1 - eps) + (tau - 1/2)),
+ *   Om_i = f_opp(i) - f_i + w_i rho - f^eq_opp(i)(rho, u)
+ * (the bounce-back of the non-equilibrium part), then plain streaming
+ * (every node carries populations; populations leaving the x range come
+ * back reversed, as at a resting wall), then the inlet and outlet of
+ * lbm_step.  The probe averages the density over every node of its plane. */
+static void psm_step(orc_sim* s) {
+    int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
+    long N = s->N;
+    double tau = s->p.tau, sh = tau - 0.5;
+    if (!s->eps && !s->eps_auto) {
+        s->eps_auto = (double*)malloc(sizeof(double) * N);
+        orc_psm_fraction(s, s->eps_auto);
+    }
+    const double* epsv = s->eps ? s->eps : s->eps_auto;
+    if (s->p.probe_x >= 0 && s->p.probe_x < nx) {
+        double sum = 0;
+        for (int y = 0; y < ny; ++y)
+            for (int z = 0; z < nz; ++z) {
+                long n = nidx(s, s->p.probe_x, y, z);
+                for (int m = 0; m < Q; ++m) sum += s->f[m * N + n];
+            }
+        if (s->trace_len == s->trace_cap) {
+            s->trace_cap = s->trace_cap ? 2 * s->trace_cap : 1024;
+            s->trace = (double*)realloc(s->trace, sizeof(double) * s->trace_cap);
+        }
+        s->trace[s->trace_len++] = sum / ((double)ny * nz);
+    }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int x = 0; x < nx; ++x)
+        for (int y = 0; y < ny; ++y)
+            for (int z = 0; z < nz; ++z) {
+                long n = nidx(s, x, y, z);
+                double eps = epsv[n];
+                double B = eps * sh / ((1.0 - eps) + sh);
+                double fm[Q], rho, j[3], feq[Q], fs[Q];
+                for (int m = 0; m < Q; ++m) fm[m] = s->f[m * N + n];
+                moments(fm, &rho, j);
+                orc_equilibrium(rho, j[0] / rho, j[1] / rho, j[2] / rho, feq);
+                for (int m = 0; m < Q; ++m) {
+                    double om = fm[OPP[m]] - fm[m] + WT[m] * rho - feq[OPP[m]];
+                    fs[m] = fm[m] - (1.0 - B) / tau * (fm[m] - feq[m]) + B * om;
+                }
+                for (int m = 0; m < Q; ++m) {
+                    int xx = x + CX[m];
+                    if (s->px) {
+                        xx = wrapi(xx, nx);
+                    } else if (xx < 0 || xx >= nx) {
+                        s->fn[OPP[m] * N + n] = fs[m];
+                        continue;
+                    }
+                    s->fn[m * N + nidx(s, xx, wrapi(y + CY[m], ny), wrapi(z + CZ[m], nz))] = fs[m];
+                }
+            }
+    if (!s->px) {
+        long long tn = s->t + 1;
+        if (s->p.inlet == ORC_INLET_PRESSURE) {
+            double rin = orc_source_density(s, tn);
+            for (int y = 0; y < ny; ++y)
+                for (int z = 0; z < nz; ++z) {
+                    long n = nidx(s, 0, y, z);
+                    double fm[Q];
+                    for (int m = 0; m < Q; ++m) fm[m] = s->fn[m * N + n];
+                    orc_pressure_face(fm, rin, 0);
+                    for (int m = 0; m < Q; ++m) s->fn[m * N + n] = fm[m];
+                }
+        }
+        if (s->p.outlet == ORC_OUTLET_ZERO_GRADIENT && nx >= 2) {
+            for (int y = 0; y < ny; ++y)
+                for (int z = 0; z < nz; ++z) {
+                    long n = nidx(s, nx - 1, y, z), u = nidx(s, nx - 2, y, z);
+                    for (int m = 0; m < Q; ++m)
+                        if (CX[m] == -1) s->fn[m * N + n] = s->fn[m * N + u];
+                }
+        } else if (s->p.outlet == ORC_OUTLET_PRESSURE) {
+            for (int y = 0; y < ny; ++y)
+                for (int z = 0; z < nz; ++z) {
+                    long n = nidx(s, nx - 1, y, z);
+                    double fm[Q];
+                    for (int m = 0; m < Q; ++m) fm[m] = s->fn[m * N + n];
+                    orc_pressure_face(fm, s->p.rho_f, 1);
+                    for (int m = 0; m < Q; ++m) s->fn[m * N + n] = fm[m];
+                }
+        }
+    }
+    double* tmp = s->f;
+    s->f = s->fn;
+    s->fn = tmp;
+}
+
+void orc_set_coupling(orc_sim* s, int psm) { s->psm = psm ? 1 : 0; }
+
+void orc_psm_set_fraction(orc_sim* s, const double* eps) {
+    free(s->eps);
+    s->eps = NULL;
+    if (!eps) return;
+    s->eps = (double*)malloc(sizeof(double) * s->N);
+    memcpy(s->eps, eps, sizeof(double) * s->N);
+}
+
 /* ------------------------------------------------------------ public API */
 
 orc_sim* orc_create(const orc_params* p) {
@@ -844,6 +993,8 @@ int orc_set_packing(orc_sim* s, int n, const double* X, const double* R, const d
         for (int i = 0; i < s->np; ++i) free(s->pairs[i].e);
         free(s->pairs);
     }
+    free(s->eps_auto);
+    s->eps_auto = NULL;
     s->np = n;
     int nn = n > 0 ? n : 1;
     s->X = (double*)calloc(3 * nn, sizeof(double));
@@ -914,7 +1065,11 @@ int orc_set_source(orc_sim* s, int waveform, double amplitude, double omega, lon
 int orc_step(orc_sim* s, long long nsteps) {
     if (!s->have_packing) return -1;
     for (long long k = 0; k < nsteps; ++k) {
-        if (s->p.lbm_on) {
+        if (s->p.lbm_on && s->psm) {
+            memset(s->Fh, 0, sizeof(double) * 3 * s->np);
+            memset(s->Th, 0, sizeof(double) * 3 * s->np);
+            psm_step(s);
+        } else if (s->p.lbm_on) {
             lbm_step(s);
         } else {
             memset(s->Fh, 0, sizeof(double) * 3 * s->np);
@@ -937,7 +1092,7 @@ long long orc_time(const orc_sim* s) { return s->t; }
 void orc_fields(const orc_sim* s, double* rho, double* u, unsigned char* solid) {
     long N = s->N;
     for (long n = 0; n < N; ++n) {
-        int sol = s->owner[n] >= 0;
+        int sol = s->owner[n] >= 0 && !s->psm;
         if (solid) solid[n] = (unsigned char)sol;
         double fm[Q], r = 0, j[3] = {0, 0, 0};
         if (!sol) {
@@ -1018,6 +1173,8 @@ void orc_destroy(orc_sim* s) {
         free(s->plane_acc);
     }
     free(s->trace);
+    free(s->eps);
+    free(s->eps_auto);
     free(s);
 }
 

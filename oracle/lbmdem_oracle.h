@@ -48,6 +48,14 @@ void orc_destroy(orc_sim* s);
 /* 1: count the link momentum as printed in Eq. 15, c_d (f~_d + f_d*);
  * 0 (default): about the rest state, c_d (f~_d + f_d* - 2 w_d rho_f). */
 void orc_set_link_form(orc_sim* s, int literal);
+/* 1: the smooth partially-saturated surrogate coupling for gradients in the
+ * sphere positions (fixed spheres; outside the paper's chosen method);
+ * 0 (default): the momentum-exchange coupling. */
+void orc_set_coupling(orc_sim* s, int psm);
+/* The surrogate's solid fraction of every node [x][y][z]; a non-NULL eps
+ * given to orc_psm_set_fraction replaces it (NULL restores it). */
+void orc_psm_fraction(const orc_sim* s, double* eps);
+void orc_psm_set_fraction(orc_sim* s, const double* eps);
 /* OpenMP threads of every later call (results do not depend on it). */
 void orc_set_threads(int n);
 int orc_get_threads(void);

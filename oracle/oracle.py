@@ -74,6 +74,9 @@ def _load():
         lib.orc_source_density.argtypes = [C.c_void_p, ll]
         lib.orc_pair_force.argtypes = [P(_Params), d, d, P(d), P(d), d, P(d), P(d), P(d)]
         lib.orc_set_link_form.argtypes = [C.c_void_p, i]
+        lib.orc_set_coupling.argtypes = [C.c_void_p, i]
+        lib.orc_psm_fraction.argtypes = [C.c_void_p, P(d)]
+        lib.orc_psm_set_fraction.argtypes = [C.c_void_p, P(d)]
         lib.orc_set_threads.argtypes = [i]
         lib.orc_get_threads.restype = i
         _lib = lib
@@ -200,6 +203,23 @@ class Oracle:
         """True: the link momentum as printed in Eq. 15, c_d (f~_d + f_d*);
         False (default): about the rest state (the reading both sides use)."""
         _load().orc_set_link_form(self._s, 1 if literal else 0)
+
+    def set_coupling(self, psm: bool):
+        """True: the smooth partially-saturated surrogate (fixed spheres, every
+        node fluid-carrying, solid-fraction-weighted collision); False: the
+        momentum-exchange coupling of the paper (default)."""
+        _load().orc_set_coupling(self._s, 1 if psm else 0)
+
+    def psm_fraction(self):
+        """The surrogate's solid fraction per node, [nx, ny, nz]."""
+        e = np.zeros(self.N)
+        _load().orc_psm_fraction(self._s, _dp(e))
+        return e.reshape(self.w.nx, self.w.ny, self.w.nz)
+
+    def psm_set_fraction(self, eps):
+        """Replace the surrogate's solid fraction (None: back to the spheres')."""
+        e = None if eps is None else _f64(eps, (self.N,))
+        _load().orc_psm_set_fraction(self._s, _dp(e))
 
     @property
     def t(self):

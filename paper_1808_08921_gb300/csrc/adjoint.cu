@@ -203,10 +203,7 @@ __global__ void __launch_bounds__(256) k_adj_step(AdjArgs A, const float* nat, f
             out[(size_t)j * P + i] = (1.0f - om) * s[j] + om * (Aa + Bx * cx(j) + By * cy(j) + Bz * cz(j)) + add;
         dw = -(double)sw;
     }
-    const unsigned full = 0xffffffffu;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) dw += __shfl_xor_sync(full, dw, o);
-    if ((threadIdx.x & 31) == 0 && dw != 0.0) atomicAdd(d_omega, dw);
+    block_sum_to(dw, d_omega + blockIdx.x % GRAD_COPIES);
 }
 
 void launch_adj_step(const AdjArgs& A, const float* nat, float* out, float dl, double* d_omega, cudaStream_t s) {

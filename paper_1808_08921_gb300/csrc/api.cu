@@ -1470,9 +1470,9 @@ int lbm_dem_adjoint(lbmdem_ctx* c, int64_t steps, int32_t every, const double* t
     CK(adj.alloc((size_t)Q * c->nSpad));
     CK(adj2.alloc((size_t)Q * c->nSpad));
     CK(nbr.alloc((size_t)(Q - 1) * c->nSpad));
-    CK(grads.alloc(2));
+    CK(grads.alloc(GRAD_COPIES + 1));  // omega derivative copies, then the amplitude's
     CK(cudaMemsetAsync(adj.p, 0, nbytes, s));
-    CK(cudaMemsetAsync(grads.p, 0, 2 * sizeof(double), s));
+    CK(cudaMemsetAsync(grads.p, 0, (GRAD_COPIES + 1) * sizeof(double), s));
     launch_adj_nbr(make_lat(c), nbr.p, s);
     CK(cudaGetLastError());
     const int64_t t_end = c->t;
@@ -1496,7 +1496,7 @@ int lbm_dem_adjoint(lbmdem_ctx* c, int64_t steps, int32_t every, const double* t
         for (int64_t k = n - 1; k >= 0; --k) {
             int64_t t = tg + k;  // step t -> t + 1
             A.adj = adj.p;
-            launch_adj_boundary(A, source_shape(c->src, t + 1), grads.p + 1, s);
+            launch_adj_boundary(A, source_shape(c->src, t + 1), grads.p + GRAD_COPIES, s);
             float dlt = (float)(dl[(size_t)(t - t0)] * cs2 / (double)np_plane);
             launch_adj_step(A, nat.p + (size_t)Q * c->nSpad * k, adj2.p, dlt, grads.p, s);
             adj.swap(adj2);
@@ -1510,13 +1510,122 @@ int lbm_dem_adjoint(lbmdem_ctx* c, int64_t steps, int32_t every, const double* t
         unsigned long long tdev = (unsigned long long)t_end;
         CK(cudaMemcpyAsync(&c->st.p->t, &tdev, sizeof(tdev), cudaMemcpyHostToDevice, s));
     }
-    double gh[2];
+    double gh[GRAD_COPIES + 1];
     CK(cudaMemcpyAsync(gh, grads.p, sizeof(gh), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    double d_omega = 0.0;
+    for (int k = 0; k < GRAD_COPIES; ++k) d_omega += gh[k];
     if (loss) *loss = L;
     const double om = 1.0 / c->p.tau;
-    if (dL_dtau) *dL_dtau = -om * om * gh[0];  // d omega / d tau = -1 / tau^2
-    if (dL_damp) *dL_damp = gh[1];
+    if (dL_dtau) *dL_dtau = -om * om * d_omega;  // d omega / d tau = -1 / tau^2
+    if (dL_damp) *dL_damp = gh[GRAD_COPIES];
+    return lbm_dem_status(c);
+}
+
+__global__ void k_centres(Dem D, double* X) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D.n) return;
+    float4 d = D.dX[i], c = D.dXc[i];
+    X[3 * i] = D.Xref[3 * i] + (double)d.x - (double)c.x;
+    X[3 * i + 1] = D.Xref[3 * i + 1] + (double)d.y - (double)c.y;
+    X[3 * i + 2] = D.Xref[3 * i + 2] + (double)d.z - (double)c.z;
+}
+
+int lbm_dem_adjoint_psm(lbmdem_ctx* c, int64_t steps, int32_t every, const double* target, double* loss,
+                        double* dL_dtau, double* dL_damp, double* dL_dX, double* trace_out) {
+    if (!c || steps <= 0 || !target || every < 1) return fail(c, LBMDEM_ERR_INVALID_ARG, "adjoint_psm: arguments");
+    if (!c->have_packing || !c->lbm) return fail(c, LBMDEM_ERR_STATE, "adjoint_psm: needs a packing and the fluid");
+    if (c->any_mobile) return fail(c, LBMDEM_ERR_STATE, "adjoint_psm: every sphere must be fixed");
+    if (c->p.probe_x < 0) return fail(c, LBMDEM_ERR_STATE, "adjoint_psm: no probe plane");
+    if (c->p.inlet == LBMDEM_X_WALL) return fail(c, LBMDEM_ERR_STATE, "adjoint_psm: needs a pressure inlet or periodic x");
+    CK(cudaSetDevice(c->p.device));
+    cudaStream_t s = c->stream;
+    const size_t N = c->N, QN = (size_t)Q * N;
+    PsmArgs A{c->p.nx, c->p.ny, c->p.nz, c->p.inlet == LBMDEM_X_PERIODIC, c->p.inlet, c->p.outlet, c->p.probe_x,
+              (float)c->p.rho_f, (float)c->p.tau, N};
+    const int64_t nseg = (steps + every - 1) / every;
+    const int n = c->np;
+    DBuf<float> g0, g1, eps, lam0, lam1, ck, snap;
+    DBuf<double> X, trace, grads, G, dX;
+    CK(g0.alloc(QN));
+    CK(g1.alloc(QN));
+    CK(eps.alloc(N));
+    const bool grads_wanted = dL_dtau || dL_damp || dL_dX;
+    CK(ck.alloc(grads_wanted ? QN * (size_t)nseg : 1));
+    CK(snap.alloc(grads_wanted ? QN * (size_t)every : 1));
+    CK(X.alloc(3 * (size_t)std::max(n, 1)));
+    CK(trace.alloc((size_t)steps));
+    CK(grads.alloc(GRAD_COPIES + 1));  // tau derivative copies, then the amplitude's
+    CK(G.alloc(N));
+    CK(dX.alloc(3 * (size_t)std::max(n, 1)));
+    // the surrogate starts from rest at rho_f, source time 0
+    CK(cudaMemsetAsync(g0.p, 0, sizeof(float) * QN, s));
+    CK(cudaMemsetAsync(trace.p, 0, sizeof(double) * steps, s));
+    CK(cudaMemsetAsync(grads.p, 0, (GRAD_COPIES + 1) * sizeof(double), s));
+    CK(cudaMemsetAsync(G.p, 0, sizeof(double) * N, s));
+    if (n > 0) {
+        k_centres<<<(n + 127) / 128, 128, 0, s>>>(make_dem(c), X.p);
+        CK(cudaGetLastError());
+    }
+    launch_psm_eps(A, X.p, c->Rd.p, n, eps.p, s);
+    CK(cudaGetLastError());
+    // forward with a checkpoint at the start of every segment
+    for (int64_t t = 0; t < steps; ++t) {
+        if (grads_wanted && t % every == 0)
+            CK(cudaMemcpyAsync(ck.p + QN * (size_t)(t / every), g0.p, sizeof(float) * QN, cudaMemcpyDeviceToDevice, s));
+        launch_psm_probe(A, g0.p, trace.p + t, s);
+        launch_psm_step(A, g0.p, g1.p, eps.p, s);
+        launch_psm_boundary(A, g1.p, c->src, (unsigned long long)(t + 1), s);
+        g0.swap(g1);
+    }
+    CK(cudaGetLastError());
+    std::vector<double> tr((size_t)steps);
+    CK(cudaMemcpyAsync(tr.data(), trace.p, sizeof(double) * steps, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double cs2 = 1.0 / 3.0, nplane = (double)c->p.ny * c->p.nz;
+    std::vector<double> dl((size_t)steps);
+    double L = 0.0;
+    for (int64_t k = 0; k < steps; ++k) {
+        const double p = cs2 * (c->p.rho_f + tr[(size_t)k] / nplane), e = p - target[k];
+        L += e * e;
+        dl[(size_t)k] = 2.0 * e * cs2 / nplane;
+        if (trace_out) trace_out[k] = p;
+    }
+    if (loss) *loss = L;
+    if (!dL_dtau && !dL_damp && !dL_dX) return lbm_dem_status(c);  // the forward loss alone
+    // backward: recompute each segment from its checkpoint, then the adjoint
+    CK(lam0.alloc(QN));
+    CK(lam1.alloc(QN));
+    CK(cudaMemsetAsync(lam0.p, 0, sizeof(float) * QN, s));
+    for (int64_t seg = nseg - 1; seg >= 0; --seg) {
+        const int64_t tg = seg * every, m = std::min<int64_t>(every, steps - tg);
+        // the recomputed states go straight into their snapshot slots
+        CK(cudaMemcpyAsync(snap.p, ck.p + QN * (size_t)seg, sizeof(float) * QN, cudaMemcpyDeviceToDevice, s));
+        for (int64_t k = 0; k + 1 < m; ++k) {
+            float* nxt = snap.p + QN * (size_t)(k + 1);
+            launch_psm_step(A, snap.p + QN * (size_t)k, nxt, eps.p, s);
+            launch_psm_boundary(A, nxt, c->src, (unsigned long long)(tg + k + 1), s);
+        }
+        for (int64_t k = m - 1; k >= 0; --k) {
+            const int64_t t = tg + k;  // step t -> t + 1
+            launch_psm_adj_boundary(A, lam0.p, source_shape(c->src, t + 1), grads.p + GRAD_COPIES, s);
+            launch_psm_adj_step(A, lam0.p, snap.p + QN * (size_t)k, lam1.p, eps.p, (float)dl[(size_t)t], grads.p,
+                                G.p, s);
+            lam0.swap(lam1);
+        }
+        CK(cudaGetLastError());
+    }
+    launch_psm_grad_x(A, G.p, eps.p, X.p, c->Rd.p, n, dX.p, s);
+    CK(cudaGetLastError());
+    double gh[GRAD_COPIES + 1];
+    CK(cudaMemcpyAsync(gh, grads.p, sizeof(gh), cudaMemcpyDeviceToHost, s));
+    if (dL_dX && n > 0) CK(cudaMemcpyAsync(dL_dX, dX.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double d_tau = 0.0;
+    for (int k = 0; k < GRAD_COPIES; ++k) d_tau += gh[k];
+    if (loss) *loss = L;
+    if (dL_dtau) *dL_dtau = d_tau;
+    if (dL_damp) *dL_damp = gh[GRAD_COPIES];
     return lbm_dem_status(c);
 }
 

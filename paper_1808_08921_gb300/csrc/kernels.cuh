@@ -28,6 +28,47 @@ struct BC {
     const unsigned long long* t_dev;
 };
 
+// Eq. 25 and Table 2 at time t (steps completed), in FP64 (evaluated once
+// per block).
+__device__ __forceinline__ double source_drho(const Source& S, unsigned long long t) {
+    if (S.t_n >= 0 && (long long)t > S.t_n) return 0.0;
+    double ph = S.omega * (double)t;
+    switch (S.waveform) {
+        case 0: return S.amp * sin(ph);
+        case 1: return S.amp * (1.0 - cos(ph));
+        case 2: return S.amp;
+        case 3: {
+            double a = 0.5 * S.omega * ((double)t - S.t0);  // pi f (t - t0), f = omega / 2 pi
+            return S.amp * (1.0 - 2.0 * a * a) * exp(-a * a);
+        }
+    }
+    return 0.0;
+}
+
+// Section 2.4, x-normal D3Q19 pressure face on deviations.  side 0: inlet
+// (unknown c_x = +1), side 1: outlet (unknown c_x = -1).  Indices are the
+// paper's d (1-based) minus one.
+__device__ __forceinline__ void pressure_face(float g[Q], float drho_b, int side) {
+    float rest = g[18] + g[2] + g[3] + g[4] + g[5] + g[14] + g[15] + g[16] + g[17];
+    float Ny = 0.5f * (g[2] + g[14] + g[15] - g[3] - g[16] - g[17]);
+    float Nz = 0.5f * (g[4] + g[14] + g[16] - g[5] - g[15] - g[17]);
+    if (side == 0) {
+        float rux = drho_b - (rest + 2.f * (g[1] + g[10] + g[11] + g[12] + g[13]));
+        g[0] = g[1] + rux * (1.f / 3.f);
+        g[6] = g[11] + rux * (1.f / 6.f) - Ny;
+        g[7] = g[10] + rux * (1.f / 6.f) + Ny;
+        g[8] = g[13] + rux * (1.f / 6.f) - Nz;
+        g[9] = g[12] + rux * (1.f / 6.f) + Nz;
+    } else {
+        float rux = (rest + 2.f * (g[0] + g[6] + g[7] + g[8] + g[9])) - drho_b;
+        g[1] = g[0] - rux * (1.f / 3.f);
+        g[11] = g[6] - rux * (1.f / 6.f) + Ny;
+        g[10] = g[7] - rux * (1.f / 6.f) - Ny;
+        g[13] = g[8] - rux * (1.f / 6.f) + Nz;
+        g[12] = g[9] - rux * (1.f / 6.f) - Nz;
+    }
+}
+
 // Link lists for the link kernel.  Links are grouped by (sphere, direction
 // m, maybe), each group padded to whole chunks of 32 records, and each
 // sphere's groups together padded to whole LINK_WARP records, so a warp
@@ -154,4 +195,40 @@ void launch_adj_snapshot(const Lat& L, bool after_even, float* nat, cudaStream_t
 void launch_adj_nbr(const Lat& L, uint32_t* nbr, cudaStream_t s);
 void launch_adj_boundary(const AdjArgs& A, double shape, double* d_amp, cudaStream_t s);
 void launch_adj_step(const AdjArgs& A, const float* nat, float* out, float dl, double* d_omega, cudaStream_t s);
+
+// Parameter derivatives of the reverse kernels: each block sums its
+// threads' terms and adds them to one of GRAD_COPIES FP64 accumulators
+// (blockIdx % GRAD_COPIES: no long queue of atomics on one address); the
+// host adds the copies.
+constexpr int GRAD_COPIES = 64;
+__device__ __forceinline__ void block_sum_to(double v, double* dst) {
+    __shared__ double part[32];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) part[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? part[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && v != 0.0) atomicAdd(dst, v);
+    }
+}
+
+// psm.cu: the smooth surrogate of the coupling (dense lattice) and its reverse
+struct PsmArgs {
+    int nx, ny, nz, px, inlet, outlet, probe_x;
+    float rho_f, tau;
+    size_t N;  // nodes
+};
+void launch_psm_eps(const PsmArgs& A, const double* X, const double* R, int n, float* eps, cudaStream_t s);
+void launch_psm_step(const PsmArgs& A, const float* gin, float* gout, const float* eps, cudaStream_t s);
+void launch_psm_boundary(const PsmArgs& A, float* g, const Source& src, unsigned long long t1, cudaStream_t s);
+void launch_psm_probe(const PsmArgs& A, const float* g, double* out, cudaStream_t s);
+void launch_psm_adj_boundary(const PsmArgs& A, float* lam, double shape, double* d_amp, cudaStream_t s);
+void launch_psm_adj_step(const PsmArgs& A, const float* lin, const float* gt, float* lout, const float* eps, float dl,
+                         double* d_tau, double* G, cudaStream_t s);
+void launch_psm_grad_x(const PsmArgs& A, const double* G, const float* eps, const double* X, const double* R, int n,
+                       double* dX, cudaStream_t s);
 }  // namespace lbmdem

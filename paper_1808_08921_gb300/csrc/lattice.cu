@@ -349,47 +349,6 @@ void launch_collide(const Lat& L, const Mon& mon, bool odd, bool monitor, int ti
 
 // ------------------------------------------------------------ inlet / outlet
 
-// Eq. 25 and Table 2 at time t (steps completed), in FP64 (evaluated once
-// per block).
-__device__ double source_drho(const Source& S, unsigned long long t) {
-    if (S.t_n >= 0 && (long long)t > S.t_n) return 0.0;
-    double ph = S.omega * (double)t;
-    switch (S.waveform) {
-        case 0: return S.amp * sin(ph);
-        case 1: return S.amp * (1.0 - cos(ph));
-        case 2: return S.amp;
-        case 3: {
-            double a = 0.5 * S.omega * ((double)t - S.t0);  // pi f (t - t0), f = omega / 2 pi
-            return S.amp * (1.0 - 2.0 * a * a) * exp(-a * a);
-        }
-    }
-    return 0.0;
-}
-
-// Section 2.4, x-normal D3Q19 pressure face on deviations.  side 0: inlet
-// (unknown c_x = +1), side 1: outlet (unknown c_x = -1).  Indices are the
-// paper's d (1-based) minus one.
-__device__ __forceinline__ void pressure_face(float g[Q], float drho_b, int side) {
-    float rest = g[18] + g[2] + g[3] + g[4] + g[5] + g[14] + g[15] + g[16] + g[17];
-    float Ny = 0.5f * (g[2] + g[14] + g[15] - g[3] - g[16] - g[17]);
-    float Nz = 0.5f * (g[4] + g[14] + g[16] - g[5] - g[15] - g[17]);
-    if (side == 0) {
-        float rux = drho_b - (rest + 2.f * (g[1] + g[10] + g[11] + g[12] + g[13]));
-        g[0] = g[1] + rux * (1.f / 3.f);
-        g[6] = g[11] + rux * (1.f / 6.f) - Ny;
-        g[7] = g[10] + rux * (1.f / 6.f) + Ny;
-        g[8] = g[13] + rux * (1.f / 6.f) - Nz;
-        g[9] = g[12] + rux * (1.f / 6.f) + Nz;
-    } else {
-        float rux = (rest + 2.f * (g[0] + g[6] + g[7] + g[8] + g[9])) - drho_b;
-        g[1] = g[0] - rux * (1.f / 3.f);
-        g[11] = g[6] - rux * (1.f / 6.f) + Ny;
-        g[10] = g[7] - rux * (1.f / 6.f) - Ny;
-        g[13] = g[8] - rux * (1.f / 6.f) + Nz;
-        g[12] = g[9] - rux * (1.f / 6.f) - Nz;
-    }
-}
-
 template <bool AFTER_EVEN, int ST>
 __global__ void k_inlet_outlet(Lat L, BC bc) {
     auto* f = pops<ST>(L);

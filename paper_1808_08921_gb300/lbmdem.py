@@ -31,7 +31,7 @@ SYMBOLS = ("lbm_dem_default_params", "lbm_dem_init", "lbm_dem_set_packing",
            "lbm_dem_read_timing", "lbm_dem_last_error", "lbm_dem_destroy",
            "lbm_dem_batch_create", "lbm_dem_batch_set_time_limit", "lbm_dem_batch_step", "lbm_dem_batch_sync",
            "lbm_dem_batch_graph_launches", "lbm_dem_batch_last_error", "lbm_dem_batch_destroy",
-           "lbm_dem_adjoint", "lbm_dem_read_plane_means")
+           "lbm_dem_adjoint", "lbm_dem_adjoint_psm", "lbm_dem_read_plane_means")
 
 
 class Params(C.Structure):
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
     lib.lbm_dem_destroy.argtypes = [vp]
     lib.lbm_dem_destroy.restype = None
     lib.lbm_dem_adjoint.argtypes = [vp, i64, i32, P(d), P(d), P(d), P(d), P(d)]
+    lib.lbm_dem_adjoint_psm.argtypes = [vp, i64, i32, P(d), P(d), P(d), P(d), P(d), P(d)]
     lib.lbm_dem_read_plane_means.argtypes = [vp, P(d), P(d)]
     lib.lbm_dem_batch_create.argtypes = [P(vp), i32, P(vp)]
     lib.lbm_dem_batch_set_time_limit.argtypes = [vp, d]
@@ -260,6 +261,27 @@ class Sim:
         self._check(load().lbm_dem_adjoint(self._h, int(steps), int(every), _dp(tgt), C.byref(L), C.byref(dt),
                                            C.byref(da), _dp(tr)))
         return L.value, dt.value, da.value, tr
+
+    def adjoint_psm(self, steps, every, target):
+        """lbm_dem_adjoint_psm: (loss, dL/dtau, dL/damplitude, dL/dX[n, 3],
+        pressure trace) of the smooth coupling surrogate, from rest."""
+        tgt = np.ascontiguousarray(target, np.float64)
+        assert tgt.shape == (steps,)
+        L, dt, da = C.c_double(), C.c_double(), C.c_double()
+        dX = np.zeros((max(self.np, 1), 3))
+        tr = np.zeros(steps)
+        self._check(load().lbm_dem_adjoint_psm(self._h, int(steps), int(every), _dp(tgt), C.byref(L), C.byref(dt),
+                                               C.byref(da), _dp(dX), _dp(tr)))
+        return L.value, dt.value, da.value, dX[:self.np], tr
+
+    def surrogate_loss(self, steps, target):
+        """The smooth surrogate's forward loss and pressure trace alone."""
+        tgt = np.ascontiguousarray(target, np.float64)
+        L = C.c_double()
+        tr = np.zeros(steps)
+        self._check(load().lbm_dem_adjoint_psm(self._h, int(steps), 1, _dp(tgt), C.byref(L), None, None, None,
+                                               _dp(tr)))
+        return L.value, tr
 
     def close(self):
         if getattr(self, "_h", None):
