@@ -117,8 +117,9 @@ int lbm_dem_init(const lbmdem_params* p, lbmdem_ctx** out);
  * at rho_f, the time to t = 0 and the probe trace; paints the solid map
  * (Section 2.3) and builds the compact lattice, the surface and link lists,
  * the neighbour list and the initial contact forces on the GPU.
- * n = 0 gives a pure fluid.  Errors: INVALID_ARG (R <= 0, NaN, a sphere
- * wider than the periodic box allows, pair overlap >= min R), OOM, CUDA. */
+ * n = 0 gives a pure fluid.  Errors: INVALID_ARG (R <= 0, NaN, R + skin not
+ * below half a periodic box, 2 R + dem_skin wider than a periodic box, pair
+ * overlap >= min R), OOM, CUDA. */
 int lbm_dem_set_packing(lbmdem_ctx* c, int32_t n, const double* X, const double* R,
                         const double* V, const double* Omega, const uint8_t* fixed);
 

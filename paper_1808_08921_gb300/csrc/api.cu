@@ -861,18 +861,20 @@ int lbm_dem_set_packing(lbmdem_ctx* c, int32_t n, const double* X, const double*
         Rmax = std::max(Rmax, Rh[i]);
         Rmin = std::min(Rmin, Rh[i]);
     }
-    // geometry limits: a node is near at most one image of a sphere, and a
-    // sphere meets each image of a neighbour through one neighbour entry
+    // geometry limits: a node inside or within the skin of a sphere is so
+    // for one image only (R + skin below half a periodic box; the link lists
+    // then give each link the lever of its own image), and a sphere meets
+    // each image of a neighbour through one neighbour entry
     if (c->lbm && Rmax + c->skin + 3.0 >= 127.0)
         return fail(c, LBMDEM_ERR_INVALID_ARG, "R + skin must stay below 124 lattice units");
-    double lim_lbm = Rmax + c->skin + 1.5;
+    double lim_lbm = Rmax + c->skin;
     double lim_dem = 2 * Rmax + c->dem_skin;
     double Ls[3] = {(double)p.nx, (double)p.ny, (double)p.nz};
     for (int a = 0; a < 3; ++a) {
         bool per = a > 0 || px;
         if (!per || n == 0) continue;
         if (c->lbm && 2 * lim_lbm >= Ls[a])
-            return fail(c, LBMDEM_ERR_INVALID_ARG, "R + skin + 1.5 must stay below half the periodic box (axis %d)", a);
+            return fail(c, LBMDEM_ERR_INVALID_ARG, "R + skin must stay below half the periodic box (axis %d)", a);
         if (lim_dem > Ls[a])
             return fail(c, LBMDEM_ERR_INVALID_ARG, "2 R + dem_skin must not exceed the periodic box (axis %d)", a);
     }

@@ -275,13 +275,19 @@ __device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, long long t,
         else if (xs < 0 || xs >= A.L.nx) continue;
         int ys = wrapi(y + cy(m), A.L.ny), zs = wrapi(z + cz(m), A.L.nz);
         size_t li = ((size_t)xs * A.L.ny + ys) * A.L.nz + zs;
+        // the neighbour's offset from the centre in this visit's image: a
+        // periodic axis narrower than 2 (R + skin + 1.5) brings a node near
+        // two images of one sphere, and each of its links belongs to the
+        // image whose R + skin contains the neighbour (R + skin < L / 2
+        // makes that image unique), with that image's lever
+        const double bx = ax + cx(m), by = ay + cy(m), bz = az + cz(m);
+        const bool this_image = bx * bx + by * by + bz * bz < Rb * Rb;
         if (A.band[li]) {
-            double bx = ax + cx(m), by = ay + cy(m), bz = az + cz(m);
-            if (bx * bx + by * by + bz * bz < Rb * Rb) {
+            if (this_image) {
                 maybe |= 1u << m;
                 if (A.band[li] >= 2) shared |= 1u << m;
             }
-        } else if (A.owner[li] == p) {
+        } else if (A.owner[li] == p && this_image) {
             sure |= 1u << m;
         }
     }

@@ -8,7 +8,8 @@ Bars (FP32 arithmetic against FP64):
   * velocity: |u_gpu - u_ref| <= 1e-4 max |u_ref|;
   * sphere centres within 1e-6 lattice units; hydrodynamic force and
     torque (Eqs. 18-19), velocity and angular velocity within 1e-3 of their
-    largest component; orientation quaternions within 1e-5.
+    largest component (torque also of R |F|, angular velocity of |V| / R);
+    orientation quaternions within 1e-5.
 """
 import math
 
@@ -42,16 +43,23 @@ def compare_fields(g, o, rho_f=1.0, sig_tol=1e-3):
     return drho.max(), du, sig, umax
 
 
-def compare_particles(g, o, xtol=1e-6, ftol=1e-3, qtol=1e-5):
+def compare_particles(g, o, xtol=1e-6, ftol=1e-3, qtol=1e-5, R=None):
+    """Torques are measured against R |F| and angular velocities against
+    |V| / R as well as against themselves: where symmetry makes the oracle's
+    torque vanish (a chain on the box axis) the GPU's FP32 link sums leave a
+    round-off torque of that scale times 1e-7."""
     pg, po = g.particles(), o.particles()
     if len(po["X"]) == 0:
         return 0.0
     dx = np.abs(pg["X"] - po["X"]).max()
     assert dx <= xtol, dx
+    Rm = 1.0 if R is None else float(np.max(R))
+    scale = {"Fh": np.abs(po["Fh"]).max(), "V": np.abs(po["V"]).max()}
+    scale["Th"] = max(np.abs(po["Th"]).max(), Rm * scale["Fh"])
+    scale["W"] = max(np.abs(po["W"]).max(), scale["V"] / Rm)
     for k in ("Fh", "Th", "V", "W"):
-        ref = np.abs(po[k]).max()
         err = np.abs(pg[k] - po[k]).max()
-        assert err <= ftol * ref + 1e-12, (k, err, ref)
+        assert err <= ftol * scale[k] + 1e-12, (k, err, scale[k])
     assert np.abs(pg["q"] - po["q"]).max() <= qtol, np.abs(pg["q"] - po["q"]).max()
     return dx
 

@@ -149,6 +149,29 @@ def plane_wave(nx=620, ny=2, nz=2, tau=1.0, amplitude=1e-4, omega=0.03,
                     t_n=t_n, steps=steps, dem_substeps=1)
 
 
+def saturated_chain(mobile: bool, steps: int = 800, n: int = 60, R: float = 5.005, overlap: float = 0.01,
+                    dem_substeps: int = 10) -> Workload:
+    """Saturated granular chain of Section 3.2 (third and fourth benchmark):
+    the 12 x 12 x 620 fluid domain of the plane wave (tau 1, source rho' 1e-4
+    with omega 0.03 at x = 0 for t_n = 5000 steps, pressure locked to rho_f at
+    the far end), with 60 spheres of radius 5.005 at x = i (2R - 0.01),
+    i = 1..60, on the axis y = z = 6, overlapping by 0.01 at every contact;
+    Hertz normal contacts with E = 10, nu = 0.2 and no friction.  The paper
+    gives no particle density for the chain: the Table's rho_p is used.
+    mobile: every sphere free but the first and the last, which are held
+    (third benchmark; reading: the paper calls the equal overlaps of the
+    chain its rest state, disturbed only by the source or by shifting the
+    first sphere, which a chain with free ends is not: it would release its
+    precompression from both ends); else every sphere fixed (fourth
+    benchmark)."""
+    X = np.array([[i * (2 * R - overlap), 6.0, 6.0] for i in range(1, n + 1)])
+    fixed = np.zeros(n, np.uint8) if mobile else np.ones(n, np.uint8)
+    fixed[0] = fixed[-1] = 1
+    return Workload(name=f"chain{'_mobile' if mobile else '_fixed'}_12x12x620", nx=620, ny=12, nz=12,
+                    tau=1.0, outlet=OUTLET_PRESSURE, amplitude=1e-4, omega=0.03, t_n=5000, steps=steps,
+                    E_p=10.0, nu_p=0.2, mu=0.0, dem_substeps=dem_substeps, X=X, R=np.full(n, R), fixed=fixed)
+
+
 def random_small(seed: int, nx=20, ny=12, nz=12, n=4, R=2.5, tau=0.7,
                  mobile=True, vel=0.0, steps=40) -> Workload:
     """A few non-overlapping spheres at random places in a small column,
