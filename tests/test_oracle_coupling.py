@@ -384,3 +384,25 @@ def test_link_momentum_forms_differ_by_the_dry_contact_caps(golden_dir):
     assert np.abs(dF).max() > 1e-3
     assert np.abs((Fb - Fa) - dF).max() < 1e-12, (Fb - Fa, dF)
     assert np.abs((Tb - Ta) - dT).max() < 1e-11, (Tb - Ta, dT)
+
+
+def test_oracle_threads_do_not_change_results():
+    """The oracle's OpenMP loops (x-planes) form every sum in one fixed order,
+    so one thread and several give bit-identical populations and spheres on a
+    case with moving spheres, node conversions and a contact."""
+    w = workloads.random_small(11, nx=24, n=5, vel=0.02, steps=12)
+    w.X[1] = w.X[0] + np.array([0.0, 2 * w.R[0] - 0.05, 0.0])   # one overlapping pair
+    w.X[1, 1] %= w.ny
+    runs = []
+    before = oracle.threads()
+    try:
+        for n in (1, 3):
+            oracle.set_threads(n)
+            o = oracle.Oracle(w)
+            o.step(12)
+            runs.append((o.populations(), o.particles()))
+    finally:
+        oracle.set_threads(before)
+    assert np.array_equal(runs[0][0], runs[1][0])
+    for k in runs[0][1]:
+        assert np.array_equal(runs[0][1][k], runs[1][1][k]), k

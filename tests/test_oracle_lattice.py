@@ -125,6 +125,40 @@ def test_source_waveforms():
         assert s.source_density(51) == 1.0
 
 
+def test_source_waveform_properties():
+    """Eq. 25's source shapes pinned by what each waveform is for rather
+    than by its formula: the sine starts at zero rising and its spectrum peaks
+    at omega / 2 pi; the 1 - cos ramp starts at zero with zero slope (the
+    smooth start), never goes below the background, peaks at 2 rho' after
+    half a period and averages rho' over whole periods; the step holds
+    rho' from t = 0 to t_n.  A cos for 1 - cos, a sin/cos swap or omega read
+    as a frequency in cycles per step fails one of these."""
+    amp, period = 1e-3, 64.0
+    w = workloads.plane_wave()
+    w.amplitude, w.omega, w.t_n = amp, 2 * math.pi / period, -1
+    T = np.arange(0, 64 * 64)
+
+    def shape(wf):
+        w.waveform = wf
+        s = oracle.Oracle(w)
+        return np.array([s.source_density(int(t)) - 1.0 for t in T]) / amp
+
+    sn = shape(workloads.SINE)
+    assert sn[0] == 0.0 and sn[1] > 0.0
+    spec = np.abs(np.fft.rfft(sn))
+    assert abs(np.fft.rfftfreq(len(T))[spec.argmax()] - 1.0 / period) < 1e-12
+    assert abs(sn.sum()) < 1e-9
+    cs = shape(workloads.COSINE)
+    assert cs[0] == 0.0 and cs.min() >= 0.0
+    assert cs[1] < 0.01 * cs[int(period / 4)]             # zero slope at the start
+    assert abs(cs[int(period / 2)] - 2.0) < 1e-12 and cs.argmax() == int(period / 2)
+    assert abs(cs.mean() - 1.0) < 1e-12
+    st = shape(workloads.STEP)
+    assert np.all(np.abs(st - 1.0) < 1e-12)
+    w.t_n = 100
+    assert abs(shape(workloads.STEP)[100] - 1.0) < 1e-12 and shape(workloads.STEP)[101] == 0.0
+
+
 def test_ricker_pulse_shape():
     """The Ricker pulse (the sweep's added waveform, not in Table 2):
     r(t) = (1 - 2 a^2) exp(-a^2), a = pi f (t - t0), f = omega / 2 pi.  Pinned
