@@ -99,6 +99,10 @@ typedef struct {
     int32_t max_flips;    /* node conversions per step the scratch holds; 0 = auto    */
     int32_t tile;         /* threads per block of collide+stream: 64, 128 (0) or 256  */
     int32_t device;       /* CUDA device ordinal                                      */
+    int32_t link_mode;    /* 0: an even step's links (Eqs. 14-15, 18-19) are taken inside
+                             its collide+stream kernel, an odd step's by the link kernel;
+                             1: the link kernel every step.  Same results up to FP32
+                             summation order.                                          */
     void* cuda_stream;    /* cudaStream_t to issue on; NULL = a stream of the context */
 } lbmdem_params;
 
@@ -205,10 +209,11 @@ int lbm_dem_read_counters(lbmdem_ctx* c, int64_t out[10]);
  * brackets every launch group of the following steps with event pairs;
  * lbm_dem_read_timing synchronises and returns, per group, the summed
  * milliseconds and the number of launches since the last read:
- * [0] collide+stream, [1] link bounce-back, [2] map update, [3] inlet/outlet,
- * [4] DEM substeps. */
+ * [0] collide+stream of the odd steps, [1] link kernel, [2] map update,
+ * [3] inlet/outlet, [4] DEM substeps, [5] collide+stream of the even steps
+ * (with the step's links when link_mode is 0). */
 int lbm_dem_set_timing(lbmdem_ctx* c, int32_t enable);
-int lbm_dem_read_timing(lbmdem_ctx* c, double ms[5], int64_t launches[5]);
+int lbm_dem_read_timing(lbmdem_ctx* c, double ms[6], int64_t launches[6]);
 
 /* Gradient of the probe-plane pressure misfit for a fixed packing (every
  * sphere fixed; the paper's pressure p = c_s^2 rho, Section 3, at the probe

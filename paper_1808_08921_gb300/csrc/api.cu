@@ -62,7 +62,7 @@ struct DBuf {
     }
 };
 
-constexpr int NGROUP = 5;  // collide, links, map update, inlet/outlet, DEM
+constexpr int NGROUP = 6;  // collide odd, links, map update, inlet/outlet, DEM, collide even
 
 }  // namespace
 
@@ -100,6 +100,8 @@ struct lbmdem_ctx {
     DBuf<uint8_t> chunk_dir;  // direction (| flag) of every 32-record chunk
     uint32_t nwarps = 0;
     uint32_t nlink_raw = 0;  // link records before padding
+    DBuf<uint2> linkw;       // link word of every stored node (even steps' links in the collide kernel)
+    bool fused_links = false;
     DBuf<Flip> flip_rec;
     DBuf<float> flip_scratch;
     DBuf<uint8_t> flip_valid;
@@ -113,6 +115,7 @@ struct lbmdem_ctx {
     DBuf<float4> Fa, Ta;
     DBuf<float4> dX, dXc, dXb, V, Om, q, Vhb, Whb, Fc, Tc, xf;
     DBuf<float4> ab;  // [n][Q-1] per-step link terms, written by the map update
+    DBuf<float4> pk;  // [n][3] per-step sphere packets, written by the map update
     DBuf<int4> org, orgw;
     DBuf<float> R, invm, invI;
     DBuf<uint8_t> fixed;
@@ -225,6 +228,7 @@ static PartView make_part(lbmdem_ctx* c) {
     P.orgw = c->orgw.p;
     P.xf = c->xf.p;
     P.ab = c->ab.p;
+    P.pk = c->pk.p;
     P.Fh = c->Fh.p;
     P.Th = c->Th.p;
     return P;
@@ -502,6 +506,14 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
     launch_surf_fill(SA, np, s);
     CK(cudaGetLastError());
     c->nwarps = nlink / LINK_WARP;
+    // even steps take their links inside the collide kernel (link words from
+    // the owner map) unless the sphere indices do not fit a link word
+    c->fused_links = c->p.link_mode == 0 && c->nwarps > 0 && np <= LW_MAX_SPHERES;
+    if (c->fused_links) {
+        CK(c->linkw.ensure(nSpad));
+        launch_link_words(make_lat(c), c->linkw.p, s);
+        CK(cudaGetLastError());
+    }
     // conversion scratch
     uint32_t cap = c->p.max_flips > 0 ? (uint32_t)c->p.max_flips
                                       : std::min<uint32_t>(1u << 20, std::max<uint32_t>(4096u, nband / 8));
@@ -558,13 +570,16 @@ static void record_pair_end(lbmdem_ctx* c, size_t idx, cudaStream_t st = nullptr
 }
 
 // kernels one step issues: map update (4 when there is a band, else 1),
-// collide, links (if any surface entries), inlet/outlet (if any), DEM
-static int64_t kernels_per_step(const lbmdem_ctx* c) {
+// collide, links (if any surface entries and the step's links are not in the
+// collide kernel), inlet/outlet (if any), DEM
+static bool links_in_collide(const lbmdem_ctx* c, int parity) { return c->fused_links && parity == 0; }
+
+static int64_t kernels_per_step(const lbmdem_ctx* c, int parity) {
     int64_t k = 1;  // DEM
     if (c->lbm) {
         k += c->nband ? 4 : 1;
         k += c->nS ? 1 : 0;
-        k += c->nwarps ? 1 : 0;
+        k += c->nwarps && !links_in_collide(c, parity) ? 1 : 0;
         bool px = c->p.inlet == LBMDEM_X_PERIODIC;
         k += (!px && !(c->p.inlet != 0 && c->p.outlet > 1)) ? 1 : 0;
     }
@@ -579,14 +594,14 @@ static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
     cudaStream_t s = c->stream;
     bool tm = c->timing;
     size_t e = 0;
-    c->launches += kernels_per_step(c);
+    c->launches += kernels_per_step(c, parity);
     if (c->lbm) {
         Lat L = make_lat(c);
         PartView P = make_part(c);
         Band B{c->band_coord.p, c->band_cand.p, c->band_slack.p, c->nband};
         FlipBuf F{c->flip_rec.p, c->flip_scratch.p, c->flip_valid.p, c->flip_cap};
         if (tm) record_pair_begin(c, 2, e);
-        launch_map_update(L, P, B, F, c->st.p, parity == 1, parity, s);
+        launch_map_update(L, P, B, F, c->st.p, parity == 1, parity, c->fused_links ? c->linkw.p : nullptr, s);
         if (tm) record_pair_end(c, e);
         Mon mon{};
         DevStats* sd = c->st.p;
@@ -603,13 +618,19 @@ static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
             cudaMemsetAsync(sd->mon, 0, sizeof(double) * 6, s);
             cudaMemsetAsync(&sd->max_u_bits, 0, sizeof(uint32_t), s);
         }
-        if (tm) record_pair_begin(c, 0, e);
-        launch_collide(L, mon, parity == 1, monitor, c->p.tile > 0 ? c->p.tile : 128, s);
+        const bool fused = links_in_collide(c, parity);
+        if (tm) record_pair_begin(c, parity == 1 ? 0 : 5, e);
+        if (fused)
+            launch_collide_even_links(L, mon, P, c->linkw.p, monitor, c->p.tile > 0 ? c->p.tile : 128, s);
+        else
+            launch_collide(L, mon, parity == 1, monitor, c->p.tile > 0 ? c->p.tile : 128, s);
         if (tm) record_pair_end(c, e);
-        LinkLists LL{c->surf_link.p, c->warp_p.p, c->chunk_dir.p, c->nwarps};
-        if (tm) record_pair_begin(c, 1, e);
-        launch_links(L, P, LL, s);
-        if (tm) record_pair_end(c, e);
+        if (!fused) {
+            LinkLists LL{c->surf_link.p, c->warp_p.p, c->chunk_dir.p, c->nwarps};
+            if (tm) record_pair_begin(c, 1, e);
+            launch_links(L, P, LL, s);
+            if (tm) record_pair_end(c, e);
+        }
         // the inlet/outlet only needs this step's populations and the DEM only
         // this step's link sums: they run side by side, the boundary on a
         // side stream joined before the next step
@@ -768,6 +789,7 @@ void lbm_dem_default_params(lbmdem_params* p) {
     p->max_flips = 0;
     p->tile = 0;
     p->device = 0;
+    p->link_mode = 0;
     p->cuda_stream = nullptr;
 }
 
@@ -788,6 +810,7 @@ int lbm_dem_init(const lbmdem_params* pp, lbmdem_ctx** out) {
     if (!(p.E_p > 0) || !(p.nu_p > -1 && p.nu_p < 0.5) || !(p.mu >= 0) || !(p.rho_p > 0))
         return LBMDEM_ERR_INVALID_ARG;
     if (p.tile != 0 && p.tile != 64 && p.tile != 128 && p.tile != 256) return LBMDEM_ERR_INVALID_ARG;
+    if (p.link_mode != 0 && p.link_mode != 1) return LBMDEM_ERR_INVALID_ARG;
     if (p.skin < 0 || p.dem_skin < 0 || p.graph_steps < 0 || p.graph_steps % 2 || p.max_flips < 0)
         return LBMDEM_ERR_INVALID_ARG;
     int ndev = 0;
@@ -916,6 +939,7 @@ int lbm_dem_set_packing(lbmdem_ctx* c, int32_t n, const double* X, const double*
     CK(c->Tc.alloc(nn));
     CK(c->xf.alloc(nn));
     CK(c->ab.alloc((Q - 1) * nn));
+    CK(c->pk.alloc(3 * nn));
     CK(c->org.alloc(nn));
     CK(c->orgw.alloc(nn));
     CK(c->R.alloc(nn));
@@ -1350,7 +1374,8 @@ int lbm_dem_batch_step(lbmdem_batch* b, const int64_t* steps) {
         lbmdem_ctx* c = b->cols[i];
         BCK(cudaStreamWaitEvent(c->stream, b->done, 0));
         if (rem[i] <= 0) continue;
-        c->launches += kernels_per_step(c) * rem[i] + (rem[i] + 1) / 2;  // steps + loop control
+        for (int64_t k = 0; k < rem[i]; ++k) c->launches += kernels_per_step(c, (int)((c->t + k) & 1));
+        c->launches += (rem[i] + 1) / 2;  // loop control
         if (c->p.monitor_every > 0) c->mon_step = c->t + rem[i] - 1;
         c->t += rem[i];  // corrected from the device count by lbm_dem_batch_sync if a loop stopped early
         c->steps_until_check = 0;
@@ -1837,7 +1862,7 @@ int lbm_dem_set_timing(lbmdem_ctx* c, int32_t enable) {
     return 0;
 }
 
-int lbm_dem_read_timing(lbmdem_ctx* c, double ms[5], int64_t launches[5]) {
+int lbm_dem_read_timing(lbmdem_ctx* c, double ms[6], int64_t launches[6]) {
     if (!c) return LBMDEM_ERR_INVALID_ARG;
     if (int r = collect_timing(c)) return r;
     for (int g = 0; g < NGROUP; ++g) {

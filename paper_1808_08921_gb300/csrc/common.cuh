@@ -117,6 +117,13 @@ struct Lat {
 
 __device__ __forceinline__ int wrap1(int a, int L) { return a < 0 ? a + L : (a >= L ? a - L : a); }
 
+// minimum image of an offset -L < d < L
+__device__ __forceinline__ int imin_small(int d, int L) {
+    if (2 * d > L) return d - L;
+    if (2 * d < -L) return d + L;
+    return d;
+}
+
 // Compact index of node (x+dx, y+dy, z+dz) if it is fluid now, else NONE.
 // dx, dy, dz in {-1, 0, 1}.  Out-of-range x (non-periodic) returns NONE.
 __device__ __forceinline__ uint32_t fluid_index(const Lat& L, int x, int y, int z, int dx, int dy,
@@ -203,6 +210,8 @@ struct PartView {
     const int4* orgw;     // [n] that origin wrapped into the box (periodic axes)
     const float4* xf;     // [n] X(t) - origin, FP32
     float4* ab;           // [n][Q-1] moving-wall terms of the step's links (alpha - xf.beta, beta)
+    float4* pk;           // [n][3] sphere packet of the step: {xf, V.x} {V.y, V.z, W.x, W.y}
+                          // {W.z, wrapped origin as int bits}
     double* Fh;           // [NREP][n][3] hydrodynamic force accumulators (summed by the DEM)
     double* Th;           // [NREP][n][3] hydrodynamic torque accumulators
 };

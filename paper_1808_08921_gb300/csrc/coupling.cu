@@ -31,12 +31,6 @@
 
 namespace lbmdem {
 
-// minimum image of an offset -L < d < L
-__device__ __forceinline__ int imin_small(int d, int L) {
-    if (2 * d > L) return d - L;
-    if (2 * d < -L) return d + L;
-    return d;
-}
 
 
 // Directions of Eq. 3 as a constant table, read with a warp-uniform index.
@@ -251,7 +245,59 @@ struct MapArgs {
     DevStats* st;
     int par;        // parity of the step (selects the flip counter)
     int after_even; // layout of the state the step starts from
+    uint2* lw;      // link words renewed around converted nodes (null: not kept)
 };
+
+// Link word of the stored node (x, y, z) from the owner map (see LW_MASK):
+// every direction whose neighbour a sphere owns is a link (out-of-range x
+// neighbours of a non-periodic column are not).
+__device__ uint2 link_word(const Lat& L, int x, int y, int z) {
+    // every neighbour's owner is loaded before any is used
+    int own[Q - 1];
+#pragma unroll
+    for (int m = 0; m < Q - 1; ++m) {
+        int xs = x + cx(m);
+        bool in = true;
+        if (L.px) xs = wrap1(xs, L.nx);
+        else in = xs >= 0 && xs < L.nx;
+        const int ys = wrap1(y + cy(m), L.ny), zs = wrap1(z + cz(m), L.nz);
+        own[m] = in ? __ldcg(&L.owner[((size_t)xs * L.ny + ys) * L.nz + zs]) : OWNER_FLUID;
+    }
+    uint32_t mask = 0u, sel = 0u, pa = LW_NONE, pb = LW_NONE;
+    bool many = false;
+#pragma unroll
+    for (int m = 0; m < Q - 1; ++m) {
+        if (own[m] == OWNER_FLUID) continue;
+        mask |= 1u << m;
+        const uint32_t p = (uint32_t)own[m];
+        if (pa == LW_NONE || p == pa) {
+            pa = p;
+        } else if (pb == LW_NONE || p == pb) {
+            pb = p;
+            sel |= 1u << m;
+        } else {
+            many = true;
+        }
+    }
+    if (many) {
+        pa = LW_NONE;
+        pb = LW_NONE;
+        sel = 0u;
+    }
+    return make_uint2(mask | (pa << 18), sel | (pb << 18));
+}
+
+__global__ void k_link_words(Lat L, uint2* lw) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.nS) return;
+    int x, y, z;
+    unpack_coord(L.coord[i], x, y, z);
+    lw[i] = link_word(L, x, y, z);
+}
+
+void launch_link_words(const Lat& L, uint2* lw, cudaStream_t s) {
+    if (L.nS) k_link_words<<<(L.nS + 255) / 256, 256, 0, s>>>(L, lw);
+}
 
 __global__ void k_map_band(MapArgs A) {
     pdl_trigger();  // launched normally: its predecessors are the DEM and the boundary branch
@@ -281,6 +327,11 @@ __global__ void k_map_band(MapArgs A) {
             const float alpha = sw * (ex * V.x + ey * V.y + ez * V.z);
             A.P.ab[(size_t)k * (Q - 1) + m] = make_float4(alpha - (xf.x * bx + xf.y * by + xf.z * bz), bx, by, bz);
         }
+        // the same state for the even steps' links inside the collide kernel
+        const int4 o = A.P.orgw[k];
+        A.P.pk[3 * (size_t)k] = make_float4(xf.x, xf.y, xf.z, V.x);
+        A.P.pk[3 * (size_t)k + 1] = make_float4(V.y, V.z, W.x, W.y);
+        A.P.pk[3 * (size_t)k + 2] = make_float4(W.z, __int_as_float(o.x), __int_as_float(o.y), __int_as_float(o.z));
     }
     if (k >= A.band.n) return;
     // a node farther from every candidate surface (at the layout) than any
@@ -518,15 +569,35 @@ __device__ void map_commit_one(const MapArgs& A, uint32_t k) {
 }
 
 // One block per queued node: thread t < 361 writes population m = t % 19 of
-// node j = t / 19 back with the new map.
+// node j = t / 19 back with the new map; the 19 first threads of the warp
+// after those (a warp of its own, so neither path waits for the other)
+// renew the link words of the node and its 18 neighbours from the committed
+// owner map (neighbours shared by two queued nodes get the same word twice).
+constexpr int SCATTER_THREADS = MAP_THREADS + 32;
 template <int ST>
-__global__ void __launch_bounds__(MAP_THREADS) k_map_scatter(MapArgs A) {
+__global__ void __launch_bounds__(SCATTER_THREADS) k_map_scatter(MapArgs A) {
     pdl_wait();
     pdl_trigger();
     const Lat L = A.L;
     const uint32_t nf = min(A.st->nflip[A.par], A.F.cap);
     const int t = threadIdx.x, j = t / Q, m = t % Q;
-    if (t >= Q * Q) return;
+    if (t >= Q * Q) {
+        const int jn = t - MAP_THREADS;  // 0 ... 17: neighbour x + c_jn, 18: the node
+        if (jn < 0) return;
+        if (A.lw == nullptr || jn >= Q) return;
+        for (uint32_t w = blockIdx.x; w < nf; w += gridDim.x) {
+            int x, y, z;
+            unpack_coord(A.F.rec[w].coord, x, y, z);
+            int xs = x + cx(jn);
+            if (L.px) xs = wrap1(xs, L.nx);
+            else if (xs < 0 || xs >= L.nx) continue;
+            const int ys = wrap1(y + cy(jn), L.ny), zs = wrap1(z + cz(jn), L.nz);
+            bool fl;
+            const uint32_t ci = stored_index(L, xs, ys, zs, fl);
+            if (ci != NONE) A.lw[ci] = link_word(L, xs, ys, zs);
+        }
+        return;
+    }
     for (uint32_t w = blockIdx.x; w < nf; w += gridDim.x) {
         if (!A.F.valid[(size_t)w * Q + j]) continue;
         const Flip f = A.F.rec[w];
@@ -542,8 +613,8 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map_scatter(MapArgs A) {
 }
 
 void launch_map_update(const Lat& L, const PartView& P, const Band& band, const FlipBuf& F,
-                       DevStats* st, bool after_even, int step_parity, cudaStream_t s) {
-    MapArgs A{L, P, band, F, st, step_parity, after_even ? 1 : 0};
+                       DevStats* st, bool after_even, int step_parity, uint2* lw, cudaStream_t s) {
+    MapArgs A{L, P, band, F, st, step_parity, after_even ? 1 : 0, lw};
     uint32_t nb = band.n > (uint32_t)P.n ? band.n : (uint32_t)P.n;
     if (nb == 0) nb = 1;
     k_map_band<<<(nb + 255) / 256, 256, 0, s>>>(A);
@@ -554,9 +625,10 @@ void launch_map_update(const Lat& L, const PartView& P, const Band& band, const 
     else if (L.st == 1) launch_pdl(k_map_gather_convert<1>, grid, MAP_THREADS, s, A);
     else launch_pdl(k_map_gather_convert<2>, grid, MAP_THREADS, s, A);
     launch_pdl(k_map_commit, grid, 256, s, A);
-    if (L.st == 0) launch_pdl(k_map_scatter<0>, grid, MAP_THREADS, s, A);
-    else if (L.st == 1) launch_pdl(k_map_scatter<1>, grid, MAP_THREADS, s, A);
-    else launch_pdl(k_map_scatter<2>, grid, MAP_THREADS, s, A);
+    const unsigned sthreads = lw ? SCATTER_THREADS : MAP_THREADS;
+    if (L.st == 0) launch_pdl(k_map_scatter<0>, grid, sthreads, s, A);
+    else if (L.st == 1) launch_pdl(k_map_scatter<1>, grid, sthreads, s, A);
+    else launch_pdl(k_map_scatter<2>, grid, sthreads, s, A);
 }
 
 }  // namespace lbmdem

@@ -101,6 +101,18 @@ struct LinkLists {
     uint32_t nwarps;
 };
 
+// Link word of a stored node, for the even steps' links inside the collide
+// kernel (one 8-byte word per node):
+//   .x = link mask (bit m, m < 18: the neighbour x + c_m is solid) | sphere A << 18
+//   .y = B mask (bit m: that link's neighbour belongs to sphere B) | sphere B << 18
+// Sphere indices take 14 bits; LW_NONE stands for no sphere B, and as sphere
+// A for a node whose solid neighbours belong to more than two spheres (its
+// links then read the owner map).  Built at the layout from the owner map
+// and renewed for every converted node and its 18 neighbours.
+constexpr uint32_t LW_MASK = (1u << 18) - 1u;
+constexpr uint32_t LW_NONE = 0x3fffu;
+constexpr int LW_MAX_SPHERES = (int)LW_NONE;  // sphere indices 0 .. LW_NONE - 1
+
 // Nodes whose solid/fluid status can change before the next re-layout.
 struct Band {
     const uint32_t* coord;  // packed x, y, z
@@ -172,6 +184,8 @@ struct Dem {
 
 // lattice.cu
 void launch_collide(const Lat& L, const Mon& mon, bool odd, bool monitor, int tile, cudaStream_t s);
+void launch_collide_even_links(const Lat& L, const Mon& mon, const PartView& P, const uint2* lw, bool monitor,
+                               int tile, cudaStream_t s);
 void launch_inlet_outlet(const Lat& L, const BC& bc, bool after_even, cudaStream_t s);
 void launch_plane_sums(const Lat& L, bool after_even, double* out, cudaStream_t s);
 void launch_read_fields(const Lat& L, bool after_even, double* rho, double* u, uint8_t* solid,
@@ -180,7 +194,8 @@ void launch_read_fields(const Lat& L, bool after_even, double* rho, double* u, u
 // coupling.cu
 void launch_links(const Lat& L, const PartView& P, const LinkLists& B, cudaStream_t s);
 void launch_map_update(const Lat& L, const PartView& P, const Band& band, const FlipBuf& F,
-                       DevStats* st, bool after_even, int step_parity, cudaStream_t s);
+                       DevStats* st, bool after_even, int step_parity, uint2* lw, cudaStream_t s);
+void launch_link_words(const Lat& L, uint2* lw, cudaStream_t s);
 
 // dem.cu
 void launch_dem_step(const Dem& D, bool init_only, cudaStream_t s);

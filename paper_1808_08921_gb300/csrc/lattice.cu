@@ -197,6 +197,233 @@ __global__ void __launch_bounds__(256) k_collide_even(Lat L, Mon mon) {
     mon_flush<MON>(a, mon, true);
 }
 
+// ---- even step with the step's links (one node per thread)
+//
+// The even step is node-local, so the links of a node can be bounced where
+// its post-collision values are written.  For a link direction m of fluid
+// node x (x + c_m solid, owned by sphere p) the value leaving towards the
+// wall, g~_m, goes to slot opp(m) of x as g~_m - delta (Eq. 14, moving wall),
+//     delta = 6 w_m rho_f c_m . U,   U = V + W x r,   r = x - X,
+// the wall velocity at x (the half-link offset c_m / 2 drops out because
+// c_m . (W x c_m) = 0), and adds the link force c_m (2 g~_m - delta) of
+// Eq. 15 (counted about the rest state, as the link kernel does) and its
+// torque r x c_m (2 g~_m - delta) of Eq. 19 to the sphere.  Each thread keeps
+// two (sphere, force, torque) slots; at the end the warp sums the slots
+// sphere by sphere and adds each sum with one FP64 atomic per component.
+
+struct LinkSlot {
+    int p;
+    float v[6];  // force xyz, torque xyz
+};
+
+__device__ __forceinline__ void slot_put(LinkSlot& s, int p, const float v[6]) {
+    if (s.p < 0) {
+        s.p = p;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s.v[c] = v[c];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s.v[c] += v[c];
+    }
+}
+
+__device__ __forceinline__ void slot_add(LinkSlot& s0, LinkSlot& s1, const PartView& P, int p, const float v[6],
+                                         uint32_t rep) {
+    if (s0.p == p || s0.p < 0) {
+        slot_put(s0, p, v);
+    } else if (s1.p == p || s1.p < 0) {
+        slot_put(s1, p, v);
+    } else {  // a third sphere: add the second slot to the sums and reuse it
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            atomicAdd(P.Fh + 3 * ((size_t)rep * P.n + s1.p) + c, (double)s1.v[c]);
+            atomicAdd(P.Th + 3 * ((size_t)rep * P.n + s1.p) + c, (double)s1.v[c + 3]);
+        }
+        s1.p = -1;
+        slot_put(s1, p, v);
+    }
+}
+
+// The links of node (x, y, z) to sphere p (bit m of msk: direction m).
+__device__ __forceinline__ void node_links(const Lat& L, const PartView& P, int x, int y, int z, int p, uint32_t msk,
+                                           float g[Q], float out[6]) {
+    const float4 a = P.pk[3 * (size_t)p], b = P.pk[3 * (size_t)p + 1], c = P.pk[3 * (size_t)p + 2];
+    const int ox = __float_as_int(c.y), oy = __float_as_int(c.z), oz = __float_as_int(c.w);
+    const int ix = L.px ? imin_small(x - ox, L.nx) : x - ox;
+    const int iy = imin_small(y - oy, L.ny), iz = imin_small(z - oz, L.nz);
+    const float rx = (float)ix - a.x, ry = (float)iy - a.y, rz = (float)iz - a.z;
+    const float Ux = a.w + (b.w * rz - c.x * ry), Uy = b.x + (c.x * rx - b.z * rz), Uz = b.y + (b.z * ry - b.w * rx);
+    const float s6 = 6.0f * L.rho_f;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+#pragma unroll
+    for (int m = 0; m < Q - 1; ++m) {
+        if (!((msk >> m) & 1u)) continue;
+        const float cu = (float)cx(m) * Ux + (float)cy(m) * Uy + (float)cz(m) * Uz;
+        const float d = (s6 * wt(m)) * cu;
+        const float v = g[m];
+        g[m] = v - d;
+        const float q = 2.0f * v - d;
+        if (cx(m)) fx += cx(m) > 0 ? q : -q;
+        if (cy(m)) fy += cy(m) > 0 ? q : -q;
+        if (cz(m)) fz += cz(m) > 0 ? q : -q;
+    }
+    out[0] = fx;
+    out[1] = fy;
+    out[2] = fz;
+    out[3] = ry * fz - rz * fy;
+    out[4] = rz * fx - rx * fz;
+    out[5] = rx * fy - ry * fx;
+}
+
+// owner of the neighbour x + c_m (a link direction, so in range)
+__device__ __forceinline__ int neighbour_owner(const Lat& L, int x, int y, int z, int m) {
+    int xs = x + cx(m);
+    if (L.px) xs = wrap1(xs, L.nx);
+    const int ys = wrap1(y + cy(m), L.ny), zs = wrap1(z + cz(m), L.nz);
+    return L.owner[((size_t)xs * L.ny + ys) * L.nz + zs];
+}
+
+template <int ST> __device__ __forceinline__ float ld1(const typename PopT<ST>::T* p, float fsi) {
+    return to_f<ST>(*p, fsi);
+}
+template <> __device__ __forceinline__ float ld1<0>(const float* p, float) { return __ldcs(p); }
+template <int ST> __device__ __forceinline__ void st1(typename PopT<ST>::T* p, float v, float fs) {
+    *p = from_f<ST>(v, fs);
+}
+template <> __device__ __forceinline__ void st1<0>(float* p, float v, float) { __stcs(p, v); }
+
+template <bool MON, int ST>
+__global__ void __launch_bounds__(256, 3) k_collide_even_links(Lat L, Mon mon, PartView P, const uint2* __restrict__ lwp) {
+    pdl_wait();
+    pdl_trigger();
+    auto* f = pops<ST>(L);
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t rep = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % NREP;
+    MonAcc a = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    LinkSlot s0, s1;
+    s0.p = s1.p = -1;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s0.v[c] = s1.v[c] = 0.f;
+    if (i < L.nS && fluid_bit(L, i)) {
+        float g[Q];
+#pragma unroll
+        for (int m = 0; m < Q; ++m) g[m] = ld1<ST>(f + (size_t)m * L.nSpad + i, L.fsi);
+        const uint2 w = __ldg(&lwp[i]);
+        const uint32_t cw = __ldg(&L.coord[i]);
+        float drho, jx, jy, jz;
+        bgk(g, L.tau_inv, L.rho_f, drho, jx, jy, jz);
+        if (MON) mon_add(a, drho, jx, jy, jz, L.rho_f);
+        if ((i >= mon.pA0 && i < mon.pA1) || (i >= mon.pB0 && i < mon.pB1)) {
+            a.pdrho += drho;
+            a.pcnt += 1.f;
+        }
+        const uint32_t mask = w.x & LW_MASK;
+        if (mask) {
+            int x, y, z;
+            unpack_coord(cw, x, y, z);
+            const uint32_t pa = w.x >> 18, pb = w.y >> 18, sel = w.y & LW_MASK;
+            float v[6];
+            if (pa != LW_NONE) {
+                node_links(L, P, x, y, z, (int)pa, mask & ~sel, g, v);
+                slot_add(s0, s1, P, (int)pa, v, rep);
+                if (sel) {
+                    node_links(L, P, x, y, z, (int)pb, sel, g, v);
+                    slot_add(s0, s1, P, (int)pb, v, rep);
+                }
+            } else {
+                // neighbours of more than two spheres: one sphere at a time
+                uint32_t rem = mask;
+                while (rem) {
+                    int p = -1;
+#pragma unroll
+                    for (int m = 0; m < Q - 1; ++m)
+                        if (p < 0 && ((rem >> m) & 1u)) p = neighbour_owner(L, x, y, z, m);
+                    uint32_t sub = 0u;
+#pragma unroll
+                    for (int m = 0; m < Q - 1; ++m)
+                        if (((rem >> m) & 1u) && neighbour_owner(L, x, y, z, m) == p) sub |= 1u << m;
+                    node_links(L, P, x, y, z, p, sub, g, v);
+                    slot_add(s0, s1, P, p, v, rep);
+                    rem &= ~sub;
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < Q; ++m) st1<ST>(f + (size_t)opp(m) * L.nSpad + i, g[m], L.fs);
+    }
+    // the warp's slots, sphere by sphere: lanes holding the sphere contribute
+    const unsigned full = 0xffffffffu;
+    const uint32_t lane = threadIdx.x & 31;
+    for (;;) {
+        const int mine = s0.p >= 0 ? s0.p : s1.p;
+        const unsigned act = __ballot_sync(full, mine >= 0);
+        if (!act) break;
+        const int p = __shfl_sync(full, mine, __ffs(act) - 1);
+        float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (s0.p == p) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) s8[c] += s0.v[c];
+            s0.p = -1;
+        }
+        if (s1.p == p) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) s8[c] += s1.v[c];
+            s1.p = -1;
+        }
+        // transposing butterfly (lane l ends with component 4 b4 + 2 b3 + b2)
+        {
+            const bool up = lane & 16;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float keep = up ? s8[c + 4] : s8[c], send = up ? s8[c] : s8[c + 4];
+                s8[c] = keep + __shfl_xor_sync(full, send, 16);
+            }
+        }
+        {
+            const bool up = lane & 8;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float keep = up ? s8[c + 2] : s8[c], send = up ? s8[c] : s8[c + 2];
+                s8[c] = keep + __shfl_xor_sync(full, send, 8);
+            }
+        }
+        {
+            const bool up = lane & 4;
+            const float keep = up ? s8[1] : s8[0], send = up ? s8[0] : s8[1];
+            s8[0] = keep + __shfl_xor_sync(full, send, 4);
+        }
+        s8[0] += __shfl_xor_sync(full, s8[0], 2);
+        s8[0] += __shfl_xor_sync(full, s8[0], 1);
+        const int comp = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        if ((lane & 3) == 0 && comp < 6) {
+            const size_t r = (size_t)rep * P.n + p;
+            double* dst = comp < 3 ? P.Fh + 3 * r + comp : P.Th + 3 * r + (comp - 3);
+            atomicAdd(dst, (double)s8[0]);
+        }
+    }
+    mon_flush<MON>(a, mon, true);
+}
+
+template <int ST>
+static void launch_even_links_st(const Lat& L, const Mon& mon, const PartView& P, const uint2* lw, bool monitor,
+                                 int tile, cudaStream_t s) {
+    const uint32_t blocks = (L.nS + tile - 1) / tile;
+    if (monitor)
+        launch_pdl(k_collide_even_links<true, ST>, blocks, tile, s, L, mon, P, lw);
+    else
+        launch_pdl(k_collide_even_links<false, ST>, blocks, tile, s, L, mon, P, lw);
+}
+
+void launch_collide_even_links(const Lat& L, const Mon& mon, const PartView& P, const uint2* lw, bool monitor,
+                               int tile, cudaStream_t s) {
+    if (L.nS == 0) return;
+    switch (L.st) {
+        case 0: launch_even_links_st<0>(L, mon, P, lw, monitor, tile, s); break;
+        case 1: launch_even_links_st<1>(L, mon, P, lw, monitor, tile, s); break;
+        default: launch_even_links_st<2>(L, mon, P, lw, monitor, tile, s); break;
+    }
+}
+
 // compact index of bit `bit` of a word record if that node is fluid now
 __device__ __forceinline__ uint32_t word_index(const uint4& r, const uint32_t* mBp, uint32_t bit) {
     if (!(r.x & bit)) return NONE;

@@ -46,7 +46,7 @@ class Params(C.Structure):
                 ("skin", C.c_double), ("dem_skin", C.c_double),
                 ("monitor_every", C.c_int32), ("graph_steps", C.c_int32),
                 ("max_flips", C.c_int32), ("tile", C.c_int32), ("device", C.c_int32),
-                ("cuda_stream", C.c_void_p)]
+                ("link_mode", C.c_int32), ("cuda_stream", C.c_void_p)]
 
 
 class LbmDemError(RuntimeError):
@@ -240,10 +240,10 @@ class Sim:
         self._check(load().lbm_dem_set_timing(self._h, 1 if on else 0))
 
     def timing(self):
-        ms = np.zeros(5)
-        n = np.zeros(5, np.int64)
+        ms = np.zeros(6)
+        n = np.zeros(6, np.int64)
         self._check(load().lbm_dem_read_timing(self._h, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64))))
-        names = ("collide_stream", "links", "map_update", "inlet_outlet", "dem")
+        names = ("collide_odd", "links", "map_update", "inlet_outlet", "dem", "collide_even")
         return {k: (float(a), int(b)) for k, a, b in zip(names, ms, n)}
 
     def plane_means(self):

@@ -46,7 +46,7 @@ def test_profiled_traffic_only_for_the_profiled_code(tmp_path, monkeypatch):
     prof.write_text(f"kernel_source_hash: {h}\ndram_bytes_per_launch[links]: 123000000\n")
     monkeypatch.setattr(bench, "PROFILE", str(prof))
     assert bench._profiled_traffic("links") == 123e6
-    assert bench._profiled_traffic("collide_stream") is None
+    assert bench._profiled_traffic("collide_odd") is None
     prof.write_text("kernel_source_hash: 0000000000000000\ndram_bytes_per_launch[links]: 123000000\n")
     assert bench._profiled_traffic("links") is None
 
@@ -127,8 +127,8 @@ class _FakeSim:
         pass
 
     def timing(self):
-        return {"collide_stream": (20 * 0.130, 20), "links": (20 * 0.150, 20), "map_update": (0.8, 20),
-                "inlet_outlet": (0.2, 20), "dem": (0.7, 20)}
+        return {"collide_odd": (10 * 0.170, 10), "links": (10 * 0.150, 10), "map_update": (0.8, 20),
+                "inlet_outlet": (0.2, 20), "dem": (0.7, 20), "collide_even": (10 * 0.200, 10)}
 
     def status(self):
         return 0
