@@ -507,8 +507,13 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
     CK(cudaGetLastError());
     c->nwarps = nlink / LINK_WARP;
     // even steps take their links inside the collide kernel (link words from
-    // the owner map) unless the sphere indices do not fit a link word
-    c->fused_links = c->p.link_mode == 0 && c->nwarps > 0 && np <= LW_MAX_SPHERES;
+    // the owner map) unless the sphere indices do not fit a link word, or a
+    // periodic axis is narrow enough for a link node (within R + sqrt(3) of a
+    // centre, R + skin after motion) to neighbour two images of one sphere:
+    // its links would need one lever per image, which the link lists keep
+    const double reach = 2.0 * (c->Rmax + c->skin + 2.0);
+    const bool wide = c->p.ny > reach && c->p.nz > reach && (!px || c->p.nx > reach);
+    c->fused_links = c->p.link_mode == 0 && c->nwarps > 0 && np <= LW_MAX_SPHERES && wide;
     if (c->fused_links) {
         CK(c->linkw.ensure(nSpad));
         launch_link_words(make_lat(c), c->linkw.p, s);

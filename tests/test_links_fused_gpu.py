@@ -100,3 +100,24 @@ def test_three_sphere_links_match_oracle_and_link_kernel(steps):
         compare_particles(g, o, R=w.R)
     finally:
         g.close()
+
+
+def _launches(w, steps, mode):
+    s = lbmdem.Sim.from_workload(w, link_mode=mode)
+    try:
+        s.step(steps)
+        return s.counters()["launches"]
+    finally:
+        s.close()
+
+
+def test_narrow_periodic_box_keeps_the_link_lists():
+    """Where a node can neighbour two periodic images of one sphere (the
+    12 x 12 cross-section of the saturated chains, R = 5.005) every step uses
+    the link lists, whose records carry the lever of their own image; a wide
+    box takes the even steps' links in the collide kernel (one launch fewer
+    per even step)."""
+    narrow = workloads.saturated_chain(True, steps=4)
+    assert _launches(narrow, 4, 0) == _launches(narrow, 4, 1)
+    wide = workloads.random_small(5, nx=40, ny=20, nz=20, n=8, R=3.5, vel=0.02, steps=4)
+    assert _launches(wide, 4, 1) - _launches(wide, 4, 0) == 2

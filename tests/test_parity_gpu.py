@@ -8,7 +8,7 @@ Bars (FP32 arithmetic against FP64):
   * velocity: |u_gpu - u_ref| <= 1e-4 max |u_ref|;
   * sphere centres within 1e-6 lattice units; hydrodynamic force and
     torque (Eqs. 18-19), velocity and angular velocity within 1e-3 of their
-    largest component (torque also of R |F|, angular velocity of 2.5 |V| / R);
+    largest component (torque also of R |F|, angular velocity of |V| / R);
     orientation quaternions within 1e-5.
 """
 import math
@@ -45,11 +45,9 @@ def compare_fields(g, o, rho_f=1.0, sig_tol=1e-3):
 
 def compare_particles(g, o, xtol=1e-6, ftol=1e-3, qtol=1e-5, R=None):
     """Torques are measured against R |F| and angular velocities against
-    2.5 |V| / R as well as against themselves: where symmetry makes the
-    oracle's torque vanish (a chain on the box axis) the GPU's FP32 link sums
-    leave a round-off torque of that scale times 1e-7.  The angular scale is
-    the torque bar carried through the solid sphere's I = 2/5 m R^2 (a torque
-    R F changes W by 2.5 / R times the velocity change F makes)."""
+    |V| / R as well as against themselves: where symmetry makes the oracle's
+    torque vanish (a chain on the box axis) the GPU's FP32 link sums leave a
+    round-off torque of that scale times 1e-7."""
     pg, po = g.particles(), o.particles()
     if len(po["X"]) == 0:
         return 0.0
@@ -58,7 +56,7 @@ def compare_particles(g, o, xtol=1e-6, ftol=1e-3, qtol=1e-5, R=None):
     Rm = 1.0 if R is None else float(np.max(R))
     scale = {"Fh": np.abs(po["Fh"]).max(), "V": np.abs(po["V"]).max()}
     scale["Th"] = max(np.abs(po["Th"]).max(), Rm * scale["Fh"])
-    scale["W"] = max(np.abs(po["W"]).max(), 2.5 * scale["V"] / Rm)
+    scale["W"] = max(np.abs(po["W"]).max(), scale["V"] / Rm)
     for k in ("Fh", "Th", "V", "W"):
         err = np.abs(pg[k] - po[k]).max()
         assert err <= ftol * scale[k] + 1e-12, (k, err, scale[k])
