@@ -124,12 +124,17 @@ def _code_only(text):
     return re.sub(r"\s+", "", text)
 
 
+# the sources of the profiled kernels (collide+stream of both parities, the
+# link kernel) and the headers they include; host-side launch code is not in it
+PROFILED_SOURCES = ("common.cuh", "kernels.cuh", "lattice.cu", "coupling.cu")
+
+
 def _kernel_hash():
-    """Hash of the CUDA sources' code (comments and layout excluded): a
-    profile is valid only for the code it measured."""
-    import glob
+    """Hash of the profiled kernels' source code (comments and layout
+    excluded): a profile is valid only for the code it measured."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1808_08921_gb300", "csrc", "*.cu*"))):
+    for name in PROFILED_SOURCES:
+        f = os.path.join(ROOT, "paper_1808_08921_gb300", "csrc", name)
         h.update(_code_only(open(f).read()).encode())
     return h.hexdigest()[:16]
 

@@ -99,10 +99,12 @@ typedef struct {
     int32_t max_flips;    /* node conversions per step the scratch holds; 0 = auto    */
     int32_t tile;         /* threads per block of collide+stream: 64, 128 (0) or 256  */
     int32_t device;       /* CUDA device ordinal                                      */
-    int32_t link_mode;    /* 0: an even step's links (Eqs. 14-15, 18-19) are taken inside
+    int32_t link_mode;    /* 2: an even step's links (Eqs. 14-15, 18-19) are taken inside
                              its collide+stream kernel, an odd step's by the link kernel;
-                             1: the link kernel every step.  Same results up to FP32
-                             summation order.                                          */
+                             1: the link kernel every step; 0 (default): 2 with FP32
+                             storage, 1 with 16-bit storage.  Boxes narrower than
+                             2 (R + skin + 2) on a periodic axis always take 1.  Same
+                             results up to FP32 summation order.                       */
     void* cuda_stream;    /* cudaStream_t to issue on; NULL = a stream of the context */
 } lbmdem_params;
 

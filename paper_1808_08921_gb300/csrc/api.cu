@@ -513,7 +513,11 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
     // its links would need one lever per image, which the link lists keep
     const double reach = 2.0 * (c->Rmax + c->skin + 2.0);
     const bool wide = c->p.ny > reach && c->p.nz > reach && (!px || c->p.nx > reach);
-    c->fused_links = c->p.link_mode == 0 && c->nwarps > 0 && np <= LW_MAX_SPHERES && wide;
+    // (link_mode 0: with FP32 storage only; with 16-bit storage the even
+    // collide kernel is bandwidth-light and the separate kernels measured
+    // faster)
+    const bool want = c->p.link_mode == 2 || (c->p.link_mode == 0 && c->p.storage == LBMDEM_F32);
+    c->fused_links = want && c->nwarps > 0 && np <= LW_MAX_SPHERES && wide;
     if (c->fused_links) {
         CK(c->linkw.ensure(nSpad));
         launch_link_words(make_lat(c), c->linkw.p, s);
@@ -815,7 +819,7 @@ int lbm_dem_init(const lbmdem_params* pp, lbmdem_ctx** out) {
     if (!(p.E_p > 0) || !(p.nu_p > -1 && p.nu_p < 0.5) || !(p.mu >= 0) || !(p.rho_p > 0))
         return LBMDEM_ERR_INVALID_ARG;
     if (p.tile != 0 && p.tile != 64 && p.tile != 128 && p.tile != 256) return LBMDEM_ERR_INVALID_ARG;
-    if (p.link_mode != 0 && p.link_mode != 1) return LBMDEM_ERR_INVALID_ARG;
+    if (p.link_mode < 0 || p.link_mode > 2) return LBMDEM_ERR_INVALID_ARG;
     if (p.skin < 0 || p.dem_skin < 0 || p.graph_steps < 0 || p.graph_steps % 2 || p.max_flips < 0)
         return LBMDEM_ERR_INVALID_ARG;
     int ndev = 0;

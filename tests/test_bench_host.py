@@ -36,6 +36,10 @@ def test_kernel_hash_follows_code_not_comments(tmp_path, monkeypatch):
     assert bench._kernel_hash() == h0
     f.write_text(f.read_text() + "\nstatic int unused_probe_value = 1;\n")
     assert bench._kernel_hash() != h0
+    h1 = bench._kernel_hash()
+    g = dst / "api.cu"  # host-side launch code: not a profiled kernel
+    g.write_text(g.read_text() + "\nstatic int unused_host_value = 1;\n")
+    assert bench._kernel_hash() == h1
 
 
 def test_profiled_traffic_only_for_the_profiled_code(tmp_path, monkeypatch):

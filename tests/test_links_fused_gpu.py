@@ -22,8 +22,8 @@ from test_parity_gpu import compare_fields, compare_particles
 pytestmark = pytest.mark.gpu
 
 
-def _run(w, steps, mode):
-    s = lbmdem.Sim.from_workload(w, link_mode=mode)
+def _run(w, steps, mode, **over):
+    s = lbmdem.Sim.from_workload(w, link_mode=mode, **over)
     try:
         s.step(steps)
         return s.fields(), s.particles(), s.counters(), s.status()
@@ -31,20 +31,24 @@ def _run(w, steps, mode):
         s.close()
 
 
-def _close(a, b, R):
+def _close(a, b, R, bars=(2e-6, 2e-5, 1e-6, 2e-5)):
+    """The two link paths against each other.  bars: density as a fraction of
+    the density signal, velocity of max |u|, centres in lu, force and torque
+    of their largest component; the default is FP32 summation order."""
+    br, bu, bx, bf = bars
     (rg, ug, sg), pa, ca, sta = a
     (ro, uo, so), pb, cb, stb = b
     assert sta == 0 and stb == 0
     assert np.array_equal(sg, so)
     fl = so == 0
-    assert np.abs(rg - ro)[fl].max() <= 2e-6 * max(np.abs(ro[fl] - 1.0).max(), 1e-6)
-    assert np.abs(ug - uo).max() <= 2e-5 * np.abs(uo).max() + 1e-12
+    assert np.abs(rg - ro)[fl].max() <= br * max(np.abs(ro[fl] - 1.0).max(), 1e-6)
+    assert np.abs(ug - uo).max() <= bu * np.abs(uo).max() + 1e-12
     if len(pa["X"]):
-        assert np.abs(pa["X"] - pb["X"]).max() <= 1e-6
+        assert np.abs(pa["X"] - pb["X"]).max() <= bx
         fs = np.abs(pb["Fh"]).max()
-        assert np.abs(pa["Fh"] - pb["Fh"]).max() <= 2e-5 * fs + 1e-12
+        assert np.abs(pa["Fh"] - pb["Fh"]).max() <= bf * fs + 1e-12
         ts = max(np.abs(pb["Th"]).max(), R * fs)
-        assert np.abs(pa["Th"] - pb["Th"]).max() <= 2e-5 * ts + 1e-12
+        assert np.abs(pa["Th"] - pb["Th"]).max() <= bf * ts + 1e-12
     assert ca["conversions"] == cb["conversions"]
 
 
@@ -102,8 +106,8 @@ def test_three_sphere_links_match_oracle_and_link_kernel(steps):
         g.close()
 
 
-def _launches(w, steps, mode):
-    s = lbmdem.Sim.from_workload(w, link_mode=mode)
+def _launches(w, steps, mode, **over):
+    s = lbmdem.Sim.from_workload(w, link_mode=mode, **over)
     try:
         s.step(steps)
         return s.counters()["launches"]
@@ -121,3 +125,27 @@ def test_narrow_periodic_box_keeps_the_link_lists():
     assert _launches(narrow, 4, 0) == _launches(narrow, 4, 1)
     wide = workloads.random_small(5, nx=40, ny=20, nz=20, n=8, R=3.5, vel=0.02, steps=4)
     assert _launches(wide, 4, 1) - _launches(wide, 4, 0) == 2
+    # the default takes the link kernel with 16-bit storage; mode 2 forces the
+    # collide kernel's links there too
+    f16 = dict(storage=lbmdem.F16_DEV)
+    assert _launches(wide, 4, 0, **f16) == _launches(wide, 4, 1, **f16)
+    assert _launches(wide, 4, 1, **f16) - _launches(wide, 4, 2, **f16) == 2
+
+
+# 16-bit storage rounds the two paths' slightly different FP32 values to
+# different 16-bit neighbours now and then, so the paths differ by the
+# storage's own rounding noise: the field bars of test_storage_gpu (density
+# of the signal, velocity of max |u|), ten times its centre bars (these
+# light R = 3.5 spheres move with the link sums' 16-bit noise within 21
+# steps: measured 1.6e-6 lu FP16, 1.0e-5 lu BF16) and ten times the density
+# bar for the link sums
+BARS16 = {"F16_DEV": (2e-3, 1e-1, 1e-5, 2e-2), "BF16_DEV": (2e-2, 5e-1, 1e-4, 2e-1)}
+
+
+@pytest.mark.parametrize("storage", ["F16_DEV", "BF16_DEV"])
+def test_links_in_collide_with_16_bit_storage(storage):
+    """The collide kernel's links on 16-bit populations (link_mode 2) against
+    the link kernel on the same storage."""
+    w = workloads.random_small(5, nx=40, ny=20, nz=20, n=8, R=3.5, vel=0.02, steps=21)
+    st = dict(storage=getattr(lbmdem, storage))
+    _close(_run(w, 21, 2, **st), _run(w, 21, 1, **st), 3.5, BARS16[storage])
