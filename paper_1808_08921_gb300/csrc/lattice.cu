@@ -292,18 +292,26 @@ template <int ST> __device__ __forceinline__ void st1(typename PopT<ST>::T* p, f
 }
 template <> __device__ __forceinline__ void st1<0>(float* p, float v, float) { __stcs(p, v); }
 
+// Each warp takes EVEN_ROUNDS consecutive runs of 32 nodes, one node per
+// lane and run (coalesced); the lanes' sphere slots carry over from run to
+// run (neighbouring runs mostly touch the same spheres), so the warp sums
+// them once per 32 EVEN_ROUNDS nodes.
+constexpr int EVEN_ROUNDS = 2;
+
 template <bool MON, int ST>
 __global__ void __launch_bounds__(256, 3) k_collide_even_links(Lat L, Mon mon, PartView P, const uint2* __restrict__ lwp) {
     pdl_wait();
     pdl_trigger();
     auto* f = pops<ST>(L);
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t rep = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % NREP;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t rep = gw % NREP;
     MonAcc a = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     LinkSlot s0, s1;
     s0.p = s1.p = -1;
 #pragma unroll
     for (int c = 0; c < 6; ++c) s0.v[c] = s1.v[c] = 0.f;
+    for (int run = 0; run < EVEN_ROUNDS; ++run) {
+    const uint32_t i = (gw * EVEN_ROUNDS + run) * 32u + (threadIdx.x & 31);
     if (i < L.nS && fluid_bit(L, i)) {
         float g[Q];
 #pragma unroll
@@ -350,6 +358,7 @@ __global__ void __launch_bounds__(256, 3) k_collide_even_links(Lat L, Mon mon, P
         }
 #pragma unroll
         for (int m = 0; m < Q; ++m) st1<ST>(f + (size_t)opp(m) * L.nSpad + i, g[m], L.fs);
+    }
     }
     // the warp's slots, sphere by sphere: lanes holding the sphere contribute
     const unsigned full = 0xffffffffu;
@@ -407,7 +416,7 @@ __global__ void __launch_bounds__(256, 3) k_collide_even_links(Lat L, Mon mon, P
 template <int ST>
 static void launch_even_links_st(const Lat& L, const Mon& mon, const PartView& P, const uint2* lw, bool monitor,
                                  int tile, cudaStream_t s) {
-    const uint32_t blocks = (L.nS + tile - 1) / tile;
+    const uint32_t blocks = (L.nS + tile * EVEN_ROUNDS - 1) / (tile * EVEN_ROUNDS);
     if (monitor)
         launch_pdl(k_collide_even_links<true, ST>, blocks, tile, s, L, mon, P, lw);
     else
