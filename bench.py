@@ -317,6 +317,22 @@ def run_ours(args):
                 "speedup_vs_f32": round(ms / m2, 3), "status": s2.status(),
                 "note": "populations stored as 16-bit deviations f - w rho_f, FP32 arithmetic"}
             s2.close()
+        # the precision configuration's own lattice: the 16 x 16 x 128
+        # column's physics on a 64 x 64 x 512 crop (2048 spheres R 5.7)
+        wc = workloads.config_crop(steps=args.steps)
+        crop = {}
+        for name, code in (("f32", lbmdem.F32), ("f16", lbmdem.F16_DEV), ("bf16", lbmdem.BF16_DEV)):
+            s2 = lbmdem.Sim.from_workload(wc, storage=code, **over)
+            s2.step(args.warmup)
+            m2 = time_steps(torch, s2, stream, args.steps, barrier)
+            crop[name] = {"ms_per_step": round(m2 / args.steps, 4),
+                          "value": round(s2.counters()["fluid"] * args.steps / (m2 * 1e-3) / 1e6, 1),
+                          "status": s2.status()}
+            s2.close()
+        for name in ("f16", "bf16"):
+            crop[name]["speedup_vs_f32"] = round(crop["f32"]["ms_per_step"] / crop[name]["ms_per_step"], 3)
+        storage_runs["storage_crop"] = dict(crop, workload=wc.name, lattice=[wc.nx, wc.ny, wc.nz],
+                                            spheres=len(wc.R), unit=UNIT)
     clk.__exit__(None, None, None)
     # end to end through the C ABI from host buffers
     e2e = None
