@@ -12,6 +12,7 @@
  *   2. BGK collide + stream of the D3Q19 fluid (Section 2.1, Eqs. 3-8);
  *   3. moving-wall half-way bounce-back on every fluid-solid link and the
  *      hydrodynamic force and torque on each sphere (Eqs. 14-15, 18-19);
+ *      on even steps 2 and 3 can run as one kernel (link_mode below);
  *   4. the pressure inlet with the oscillating density (Section 2.4, Zou-He
  *      form for D3Q19, Eq. 25, Table 2) and the outlet;
  *   5. K velocity-Verlet substeps of the spheres with Hertz normal and
@@ -213,7 +214,8 @@ int lbm_dem_read_counters(lbmdem_ctx* c, int64_t out[10]);
  * milliseconds and the number of launches since the last read:
  * [0] collide+stream of the odd steps, [1] link kernel, [2] map update,
  * [3] inlet/outlet, [4] DEM substeps, [5] collide+stream of the even steps
- * (with the step's links when link_mode is 0). */
+ * (with the step's links where the even steps take them there: link_mode 2,
+ * or 0 with FP32 storage). */
 int lbm_dem_set_timing(lbmdem_ctx* c, int32_t enable);
 int lbm_dem_read_timing(lbmdem_ctx* c, double ms[6], int64_t launches[6]);
 
