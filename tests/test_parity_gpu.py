@@ -194,23 +194,29 @@ def test_forced_relayout_keeps_the_state():
     compare_particles(g, o)
 
 
-@pytest.mark.parametrize("workload", ["column", "plane_wave"])
+@pytest.mark.parametrize("workload", ["column", "plane_wave", "column_even_step"])
 def test_fp64_monitors_match_oracle_totals(workload):
     """The FP64 totals the GPU accumulates on monitored steps (the drift
     monitor: sum rho and sum rho u over the fluid nodes, max |u|, Eq. 7) equal
     the oracle's sums over its fluid nodes of the same state.  A monitored
     step sums the state it starts from; with fixed spheres no node converts,
-    so that is the oracle's state after the same number of completed steps."""
-    if workload == "column":
+    so that is the oracle's state after the same number of completed steps.
+    Graph-captured runs monitor their last (odd) step; five single steps
+    with monitor_every = 5 monitor step 4, an even step (whose collide
+    kernel takes the step's links)."""
+    steps, every = 48, 16
+    if workload == "plane_wave":
+        w = workloads.plane_wave(nx=200, ny=2, nz=3, amplitude=1e-3, omega=0.05, steps=48)
+    else:
         w = workloads.config_parity(steps=48)
         w.fixed = np.ones(len(w.R), np.uint8)
-    else:
-        w = workloads.plane_wave(nx=200, ny=2, nz=3, amplitude=1e-3, omega=0.05, steps=48)
-    g, o = _sim(w, monitor_every=16), oracle.Oracle(w)
-    g.step(48)
+        if workload == "column_even_step":
+            steps, every = 5, 5
+    g, o = _sim(w, monitor_every=every), oracle.Oracle(w)
+    g.step(steps)
     mon = g.monitors()
     k = int(mon[5])
-    assert k == 47
+    assert k == steps - 1
     o.step(k)
     ro, uo, so = o.fields()
     fl = so == 0
