@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) k_collide_even(Lat L, Mon mon) {
     mon_flush<MON>(a, mon, true);
 }
 
-// ---- even step with the step's links (one node per thread)
+// ---- even step with the step's links (one node per lane and 32-node run)
 //
 // The even step is node-local, so the links of a node can be bounced where
 // its post-collision values are written.  For a link direction m of fluid
