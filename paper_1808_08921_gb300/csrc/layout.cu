@@ -244,12 +244,20 @@ struct SurfNode {
     bool in_band;
 };
 
-__device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, long long t, int x0, int y0, int z0,
+// The geometry is FP32 (FP64 arithmetic is slow on this part): the offset
+// from the centre is formed in FP64 and rounded once (|offset| < 2 reach),
+// and both tests carry a relative margin of 1e-5 on squared distances, far
+// above FP32 rounding: the reach test only has to keep a superset of the
+// link nodes, and the image test separates distances below R (owned) from
+// distances above L - R - skin (another image), both at least the skin away
+// from R + skin.
+__device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, uint32_t t, int x0, int y0, int z0,
                                           int ey, int ez, SurfNode& sn) {
-    int zi = z0 + (int)(t % ez);
-    long long r = t / ez;
-    int yi = y0 + (int)(r % ey);
-    int xi = x0 + (int)(r / ey);
+    const uint32_t r = t / (uint32_t)ez;
+    int zi = z0 + (int)(t - r * (uint32_t)ez);
+    const uint32_t q = r / (uint32_t)ey;
+    int yi = y0 + (int)(r - q * (uint32_t)ey);
+    int xi = x0 + (int)q;
     int x;
     if (A.L.px) x = wrapi(xi, A.L.nx);
     else {
@@ -257,16 +265,16 @@ __device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, long long t,
         x = xi;
     }
     int y = wrapi(yi, A.L.ny), z = wrapi(zi, A.L.nz);
-    double X0 = A.X[3 * p], X1 = A.X[3 * p + 1], X2 = A.X[3 * p + 2];
-    double ax = (double)xi - X0, ay = (double)yi - X1, az = (double)zi - X2;
-    double Rp = A.R[p];
-    double reach = Rp + A.reach_extra;
-    if (ax * ax + ay * ay + az * az >= reach * reach) return false;
+    const double X0 = A.X[3 * p], X1 = A.X[3 * p + 1], X2 = A.X[3 * p + 2];
+    const float ax = (float)((double)xi - X0), ay = (float)((double)yi - X1), az = (float)((double)zi - X2);
+    const float Rp = (float)A.R[p];
+    const float reach = Rp + (float)A.reach_extra;
+    if (ax * ax + ay * ay + az * az >= reach * reach * (1.0f + 1e-5f)) return false;
     bool fl;
     uint32_t ci = stored_index(A.L, x, y, z, fl);
     if (ci == NONE) return false;
     const bool in_band = A.band[((size_t)x * A.L.ny + y) * A.L.nz + z] != 0;
-    double Rb = Rp + A.skin;
+    const float Rb2 = (Rp + (float)A.skin) * (Rp + (float)A.skin) * (1.0f + 1e-5f);
     uint32_t sure = 0, maybe = 0, shared = 0;
 #pragma unroll
     for (int m = 0; m < Q - 1; ++m) {
@@ -280,8 +288,8 @@ __device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, long long t,
         // two images of one sphere, and each of its links belongs to the
         // image whose R + skin contains the neighbour (R + skin < L / 2
         // makes that image unique), with that image's lever
-        const double bx = ax + cx(m), by = ay + cy(m), bz = az + cz(m);
-        const bool this_image = bx * bx + by * by + bz * bz < Rb * Rb;
+        const float bx = ax + (float)cx(m), by = ay + (float)cy(m), bz = az + (float)cz(m);
+        const bool this_image = bx * bx + by * by + bz * bz < Rb2;
         if (A.band[li]) {
             if (this_image) {
                 maybe |= 1u << m;
@@ -312,11 +320,11 @@ __global__ void k_surf_count(SurfArgs A) {
     int y0 = (int)ceil(A.X[3 * p + 1] - reach), y1 = (int)floor(A.X[3 * p + 1] + reach);
     int z0 = (int)ceil(A.X[3 * p + 2] - reach), z1 = (int)floor(A.X[3 * p + 2] + reach);
     int ey = y1 - y0 + 1, ez = z1 - z0 + 1;
-    long long vol = (long long)(x1 - x0 + 1) * ey * ez;
+    const uint32_t vol = (uint32_t)(x1 - x0 + 1) * (uint32_t)ey * (uint32_t)ez;
     __shared__ uint32_t cnt[LINK_GROUPS];
     if (threadIdx.x < LINK_GROUPS) cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (long long t = threadIdx.x; t < vol; t += blockDim.x) {
+    for (uint32_t t = threadIdx.x; t < vol; t += blockDim.x) {
         SurfNode sn;
         if (!surf_node(A, p, t, x0, y0, z0, ey, ez, sn)) continue;
         for (int m = 0; m < Q - 1; ++m) {
@@ -348,14 +356,14 @@ __global__ void k_surf_fill(SurfArgs A) {
     int y0 = (int)ceil(A.X[3 * p + 1] - reach), y1 = (int)floor(A.X[3 * p + 1] + reach);
     int z0 = (int)ceil(A.X[3 * p + 2] - reach), z1 = (int)floor(A.X[3 * p + 2] + reach);
     int ey = y1 - y0 + 1, ez = z1 - z0 + 1;
-    long long vol = (long long)(x1 - x0 + 1) * ey * ez;
+    const uint32_t vol = (uint32_t)(x1 - x0 + 1) * (uint32_t)ey * (uint32_t)ez;
     __shared__ uint32_t sh[LINK_GROUPS][33];
     __shared__ uint32_t run[LINK_GROUPS];
     if (threadIdx.x < LINK_GROUPS) run[threadIdx.x] = 0;
     __syncthreads();
     uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (long long t0 = 0; t0 < vol; t0 += blockDim.x) {
-        long long t = t0 + threadIdx.x;
+    for (uint32_t t0 = 0; t0 < vol; t0 += blockDim.x) {
+        const uint32_t t = t0 + threadIdx.x;
         SurfNode sn;
         bool ok = t < vol && surf_node(A, p, t, x0, y0, z0, ey, ez, sn);
         // group 2 m + 1 takes the `maybe` links of direction m, 2 m the others
