@@ -319,12 +319,13 @@ static int build_cells(lbmdem_ctx* c) {
     G.lo.y = G.lo.z = 0;
     int ncell = G.nc.x * G.nc.y * G.nc.z;
     CK(c->cell_of.ensure(np));
-    CK(c->cell_count.ensure(ncell));
+    CK(c->cell_count.ensure(ncell + 1));
+    CK(c->scan_tmp.ensure(scan_tmp_size((size_t)ncell + 1)));  // allocated at init with a lattice
     CK(c->cell_start.ensure(ncell + 1));
     CK(c->cell_fill.ensure(ncell));
     CK(c->cell_order.ensure(np));
     launch_cells(c->Xref.p, np, G, c->cell_of.p, c->cell_count.p, c->cell_start.p, c->cell_fill.p,
-                 c->cell_order.p, c->stream);
+                 c->cell_order.p, c->scan_tmp.p, c->stream);
     CK(cudaGetLastError());
     return 0;
 }

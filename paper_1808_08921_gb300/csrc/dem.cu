@@ -616,20 +616,6 @@ __global__ void k_cell_count(const double* X, int n, CellGrid G, int* cell_of, i
     atomicAdd(&count[c], 1);
 }
 
-__global__ void k_cell_scan_serial(const int* count, int* start, int* fill, int ncell) {
-    // cell counts are small (a few thousand cells); one thread is enough and
-    // keeps the order deterministic
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        int s = 0;
-        for (int c = 0; c < ncell; ++c) {
-            start[c] = s;
-            fill[c] = s;
-            s += count[c];
-        }
-        start[ncell] = s;
-    }
-}
-
 __global__ void k_cell_fill(const int* cell_of, int n, int* fill, int* order) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -746,11 +732,15 @@ __global__ void k_nb_build(NbBuild B) {
 
 
 void launch_cells(const double* X, int n, const CellGrid& G, int* cell_of, int* count, int* start,
-                  int* fill, int* order, cudaStream_t s) {
+                  int* fill, int* order, uint32_t* scan_tmp, cudaStream_t s) {
     int ncell = G.nc.x * G.nc.y * G.nc.z;
-    cudaMemsetAsync(count, 0, sizeof(int) * ncell, s);
+    // count[ncell] stays 0, so the exclusive scan of ncell + 1 counts also
+    // leaves the total in start[ncell]; the fill cursors start as a copy
+    cudaMemsetAsync(count, 0, sizeof(int) * (ncell + 1), s);
     if (n > 0) k_cell_count<<<(n + 255) / 256, 256, 0, s>>>(X, n, G, cell_of, count);
-    k_cell_scan_serial<<<1, 1, 0, s>>>(count, start, fill, ncell);
+    exclusive_scan(reinterpret_cast<const uint32_t*>(count), reinterpret_cast<uint32_t*>(start), (size_t)ncell + 1,
+                   scan_tmp, s);
+    cudaMemcpyAsync(fill, start, sizeof(int) * ncell, cudaMemcpyDeviceToDevice, s);
     if (n > 0) k_cell_fill<<<(n + 255) / 256, 256, 0, s>>>(cell_of, n, fill, order);
 }
 

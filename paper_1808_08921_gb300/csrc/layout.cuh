@@ -103,7 +103,7 @@ void launch_surf_fill(const SurfArgs& A, int n, cudaStream_t s);
 
 // dem.cu
 void launch_cells(const double* X, int n, const CellGrid& G, int* cell_of, int* count, int* start,
-                  int* fill, int* order, cudaStream_t s);
+                  int* fill, int* order, uint32_t* scan_tmp, cudaStream_t s);
 void launch_nb_build(const NbBuild& B, cudaStream_t s);
 void launch_band_cand(const BandCand& B, cudaStream_t s);
 constexpr int SLACK_HIST = 1024 + 1;  // bucket counts (+ total) of launch_band_sort
