@@ -361,8 +361,8 @@ def run_ours(args):
     if not args.no_tune and world == 1:
         from paper_1808_08921_gb300 import autotune
         sim.close()
-        r = autotune.tune(w, substeps=(1, 2, 3, 5, 10), tiles=(128,), steps=64, **{k: v for k, v in over.items()
-                                                                                    if k != "cuda_stream"})
+        r = autotune.tune(w, substeps=(1, 2, 3, 5, 10), tiles=(128,), link_modes=(), steps=64,
+                          **{k: v for k, v in over.items() if k != "cuda_stream"})
         sim = lbmdem.Sim.from_workload(w, storage=storage, **dict(over, dem_substeps=r["dem_substeps"]))
         sim.step(args.warmup)
         n2 = max(2, args.steps // 2)
@@ -535,8 +535,9 @@ def run_sweep(args):
     ws, steps = workloads.config_sweep(48)
     med = sorted(range(len(ws)), key=lambda k: ws[k].nx)[len(ws) // 2]
     over = dict(skin=0.25, dem_skin=0.5)
-    tuned = autotune.tune(ws[med], steps=96, **over) if not args.no_tune else {"dem_substeps": 10, "tile": 256}
-    over.update(dem_substeps=tuned["dem_substeps"], tile=tuned["tile"])
+    tuned = (autotune.tune(ws[med], steps=96, **over) if not args.no_tune
+             else {"dem_substeps": 10, "tile": 256, "link_mode": 0})
+    over.update(dem_substeps=tuned["dem_substeps"], tile=tuned["tile"], link_mode=tuned["link_mode"])
     out = {}
     for mode in ("batch", "sequential"):
         sims = [lbmdem.Sim.from_workload(w, **over) for w in ws]
@@ -567,7 +568,8 @@ def run_sweep(args):
             "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "sweep48_32x32xL_a16_R5.7_tau0.8", "columns": len(ws),
                        "lengths": [w.nx for w in ws], "steps": steps, "fluid_updates": upd,
-                       "dem_substeps": over["dem_substeps"], "tile": over["tile"]},
+                       "dem_substeps": over["dem_substeps"], "tile": over["tile"],
+                       "link_mode": over["link_mode"]},
             "batch": out["batch"], "sequential": out["sequential"],
             "speedup_vs_sequential": round(out["batch"]["mlups"] / max(out["sequential"]["mlups"], 1e-9), 3),
             "autotune": tuned}

@@ -1,6 +1,6 @@
 """The sweep autotuner picks the smallest DEM subcycle within tolerance of
-the reference subcycle and the fastest collide+stream tile, on scratch runs,
-and a tiled run stays in parity with the oracle."""
+the reference subcycle, the fastest collide+stream tile and the faster link
+path, on scratch runs, and a tiled run stays in parity with the oracle."""
 import numpy as np
 import pytest
 
@@ -23,6 +23,10 @@ def test_tune_column():
     chosen = [row for row in r["k_table"] if row["dem_substeps"] == r["dem_substeps"]][0]
     assert chosen["status"] == 0 and chosen["rel_err"] <= 1e-2
     assert len(r["tile_table"]) == 3 and all(t["status"] == 0 for t in r["tile_table"])
+    assert r["link_mode"] in (1, 2)
+    assert len(r["link_table"]) == 2 and all(t["status"] == 0 for t in r["link_table"])
+    fastest = min(r["link_table"], key=lambda t: t["us_per_step"])
+    assert fastest["link_mode"] == r["link_mode"]
 
 
 @pytest.mark.parametrize("tile", [64, 128])
