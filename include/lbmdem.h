@@ -98,7 +98,7 @@ typedef struct {
     int32_t monitor_every;/* accumulate FP64 mass/momentum every M steps; 0 = off     */
     int32_t graph_steps;  /* steps per captured CUDA graph (even); 0 picks 16         */
     int32_t max_flips;    /* node conversions per step the scratch holds; 0 = auto    */
-    int32_t tile;         /* threads per block of collide+stream: 64, 128 (0) or 256  */
+    int32_t tile;         /* threads per block of collide+stream: 64 (0), 128 or 256  */
     int32_t device;       /* CUDA device ordinal                                      */
     int32_t link_mode;    /* 2: an even step's links (Eqs. 14-15, 18-19) are taken inside
                              its collide+stream kernel, an odd step's by the link kernel;

@@ -631,9 +631,9 @@ static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
         const bool fused = links_in_collide(c, parity);
         if (tm) record_pair_begin(c, parity == 1 ? 0 : 5, e);
         if (fused)
-            launch_collide_even_links(L, mon, P, c->linkw.p, monitor, c->p.tile > 0 ? c->p.tile : 128, s);
+            launch_collide_even_links(L, mon, P, c->linkw.p, monitor, c->p.tile > 0 ? c->p.tile : 64, s);
         else
-            launch_collide(L, mon, parity == 1, monitor, c->p.tile > 0 ? c->p.tile : 128, s);
+            launch_collide(L, mon, parity == 1, monitor, c->p.tile > 0 ? c->p.tile : 64, s);
         if (tm) record_pair_end(c, e);
         if (!fused) {
             LinkLists LL{c->surf_link.p, c->warp_p.p, c->chunk_dir.p, c->nwarps};

@@ -1,7 +1,7 @@
 """GPU parity at full size: the 128x128x1024 column (2048 spheres R 11.4 on
 FCC a = 32, tau 0.6) in the configuration the benchmark times -- FP32
 populations, steps captured in one 16-step CUDA graph, re-layout skin 0.1,
-DEM neighbour skin 0.5, 128-thread collide+stream blocks, 10 DEM substeps --
+DEM neighbour skin 0.5, 64-thread collide+stream blocks, 10 DEM substeps --
 against the FP64 oracle on the same seeded input, over every node and every
 sphere (the oracle takes ~1.5 s per step here, so 16 steps).
 
@@ -29,7 +29,7 @@ def test_full_size_column_in_the_benchmark_configuration():
     mobile = (w.fixed == 0)[:, None]
     w.V = np.where(mobile, rng.uniform(-2e-3, 2e-3, (n, 3)), 0.0)
     w.W = np.where(mobile, rng.uniform(-2e-4, 2e-4, (n, 3)), 0.0)
-    g = lbmdem.Sim.from_workload(w, skin=0.1, dem_skin=0.5, tile=128, graph_steps=16)
+    g = lbmdem.Sim.from_workload(w, skin=0.1, dem_skin=0.5, tile=64, graph_steps=16)
     o = oracle.Oracle(w)
     g.step(16)
     o.step(16)

@@ -58,10 +58,14 @@ class _Snap:
         return self.s[3]
 
 
-@pytest.mark.parametrize("storage", [lbmdem.F32, lbmdem.F16_DEV, lbmdem.BF16_DEV])
-def test_storage_error_against_oracle(reference, storage):
+@pytest.mark.parametrize("storage,link_mode", [(lbmdem.F32, 0), (lbmdem.F16_DEV, 0), (lbmdem.BF16_DEV, 0),
+                                               (lbmdem.F16_DEV, 2), (lbmdem.BF16_DEV, 2)])
+def test_storage_error_against_oracle(reference, storage, link_mode):
+    """link_mode 0: the default path for the storage (the collide kernel's
+    links with FP32, the link kernel with 16 bits); 2: the collide kernel's
+    links on 16-bit populations."""
     w, snaps = reference
-    g = lbmdem.Sim.from_workload(w, storage=storage)
+    g = lbmdem.Sim.from_workload(w, storage=storage, link_mode=link_mode)
     done = 0
     for t in sorted(snaps):
         g.step(t - done)
@@ -74,15 +78,15 @@ def test_storage_error_against_oracle(reference, storage):
     g.close()
 
 
-@pytest.mark.parametrize("storage", [lbmdem.F16_DEV, lbmdem.BF16_DEV])
-def test_16bit_storage_through_conversions_and_relayout(storage):
+@pytest.mark.parametrize("storage,link_mode", [(lbmdem.F16_DEV, 0), (lbmdem.BF16_DEV, 0), (lbmdem.F16_DEV, 2)])
+def test_16bit_storage_through_conversions_and_relayout(storage, link_mode):
     """Spheres moving ~1 lu in a periodic box (nodes covered and uncovered,
     16-bit gather/scatter of the conversions) and a forced re-layout (the
     stored 16-bit populations move without conversion)."""
     w = workloads.random_small(1, nx=22, ny=14, nz=12, n=3, R=3.1, tau=0.8, mobile=True, vel=0.05)
     w.inlet = workloads.X_PERIODIC
     w.rho_p, w.dem_substeps = 3.0, 3
-    g = lbmdem.Sim.from_workload(w, skin=0.6, dem_skin=1.2, storage=storage)
+    g = lbmdem.Sim.from_workload(w, skin=0.6, dem_skin=1.2, storage=storage, link_mode=link_mode)
     o = oracle.Oracle(w)
     g.step(20)
     o.step(20)
