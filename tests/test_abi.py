@@ -73,6 +73,37 @@ def test_default_params_and_argument_checks_without_gpu():
     assert lib.lbm_dem_step(None, 1) == -1
 
 
+@pytest.mark.parametrize("field,value", [
+    ("nx", 0),            # a zero-length column
+    ("nx", 2),            # a pressure inlet and an outlet need three planes
+    ("probe_x", 128),     # probe plane outside the column (nx = 128)
+    ("probe_x", -2),
+    ("tau", float("nan")),
+    ("rho_f", 0.0),
+    ("dem_substeps", 0),
+    ("storage", 7),
+    ("inlet", 3),
+    ("outlet", -1),
+    ("nu_p", 0.5),        # Poisson ratio of Eqs. 11-12 below 1/2
+    ("mu", -0.1),
+    ("rho_p", 0.0),
+    ("tile", 96),
+    ("link_mode", 3),
+    ("skin", -0.1),
+    ("max_flips", -1),
+])
+def test_bad_parameters_are_refused_before_any_device_work(field, value):
+    """Corrupt parameters come back as LBMDEM_ERR_INVALID_ARG from
+    lbm_dem_init, with no context created (no GPU needed)."""
+    lib = lbmdem.load()
+    p = lbmdem.default_params()
+    p.nx, p.ny, p.nz = 128, 16, 16
+    setattr(p, field, value)
+    h = C.c_void_p()
+    assert lib.lbm_dem_init(C.byref(p), C.byref(h)) == -1
+    assert not h.value
+
+
 def test_oracle_is_not_linked_into_the_library():
     path = build.build()
     out = subprocess.check_output(["nm", "-D", "--defined-only", path], text=True)
