@@ -66,6 +66,12 @@ constexpr int NGROUP = 6;  // collide odd, links, map update, inlet/outlet, DEM,
 
 }  // namespace
 
+// cell-list buffers (per-sphere cell, per-cell counts, starts, fill cursors
+// and the spheres in cell order)
+struct CellBufs {
+    DBuf<int> of, count, start, fill, order;
+};
+
 struct lbmdem_ctx {
     lbmdem_params p{};
     std::string err;
@@ -124,7 +130,8 @@ struct lbmdem_ctx {
     DBuf<int8_t> nb_sh, nb_sh2;
     DBuf<float4> nb_dref, nb_ft, nb_dref2, nb_ft2;
     CellGrid grid{};
-    DBuf<int> cell_of, cell_count, cell_start, cell_fill, cell_order;
+    CellBufs cells;       // the DEM's cell list (cells 2 R + dem_skin wide)
+    CellBufs band_cells;  // cells R + skin wide: a band node's candidates lie within R + skin
     // stats, probe
     DBuf<DevStats> st;
     DevStats* st_host = nullptr;
@@ -294,10 +301,9 @@ static void destroy_graph(lbmdem_ctx* c) {
 
 // ------------------------------------------------------------ layout build
 
-static int build_cells(lbmdem_ctx* c) {
-    CellGrid& G = c->grid;
+// A cell list of the reference centres with cells at least h wide.
+static int build_cell_grid(lbmdem_ctx* c, CellGrid& G, double h, CellBufs& B) {
     int np = c->np;
-    double h = 2.0 * c->Rmax + c->dem_skin;
     if (h <= 0) h = 1.0;
     int px = c->p.inlet == LBMDEM_X_PERIODIC;
     G.px = px;
@@ -318,17 +324,19 @@ static int build_cells(lbmdem_ctx* c) {
     G.h.z = (double)c->p.nz / G.nc.z;
     G.lo.y = G.lo.z = 0;
     int ncell = G.nc.x * G.nc.y * G.nc.z;
-    CK(c->cell_of.ensure(np));
-    CK(c->cell_count.ensure(ncell + 1));
+    CK(B.of.ensure(np));
+    CK(B.count.ensure(ncell + 1));
     CK(c->scan_tmp.ensure(scan_tmp_size((size_t)ncell + 1)));  // allocated at init with a lattice
-    CK(c->cell_start.ensure(ncell + 1));
-    CK(c->cell_fill.ensure(ncell));
-    CK(c->cell_order.ensure(np));
-    launch_cells(c->Xref.p, np, G, c->cell_of.p, c->cell_count.p, c->cell_start.p, c->cell_fill.p,
-                 c->cell_order.p, c->scan_tmp.p, c->stream);
+    CK(B.start.ensure(ncell + 1));
+    CK(B.fill.ensure(ncell));
+    CK(B.order.ensure(np));
+    launch_cells(c->Xref.p, np, G, B.of.p, B.count.p, B.start.p, B.fill.p, B.order.p, c->scan_tmp.p, c->stream);
     CK(cudaGetLastError());
     return 0;
 }
+
+// the DEM's cells: a contact partner lies within 2 R + dem_skin
+static int build_cells(lbmdem_ctx* c) { return build_cell_grid(c, c->grid, 2.0 * c->Rmax + c->dem_skin, c->cells); }
 
 // neighbour lists from Xref; `carry` keeps the tangential history
 static int build_neighbours(lbmdem_ctx* c, bool carry) {
@@ -346,8 +354,8 @@ static int build_neighbours(lbmdem_ctx* c, bool carry) {
     B.nbmax = c->nbmax;
     B.skin = c->dem_skin;
     B.G = c->grid;
-    B.start = c->cell_start.p;
-    B.order = c->cell_order.p;
+    B.start = c->cells.start.p;
+    B.order = c->cells.order.p;
     B.cnt = c->nb_cnt2.p;
     B.nj = c->nb_j2.p;
     B.nsh = c->nb_sh2.p;
@@ -455,7 +463,9 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
     CK(c->band_cand.ensure(std::max<uint32_t>(nband, 1)));
     CK(c->band_slack.ensure(std::max<uint32_t>(nband, 1)));
     if (int r = build_cells(c)) return r;
-    BandCand BC{c->Xref.p, c->Rd.p, c->skin, c->grid, c->cell_start.p, c->cell_order.p,
+    CellGrid Gb{};
+    if (int r = build_cell_grid(c, Gb, c->Rmax + c->skin, c->band_cells)) return r;
+    BandCand BC{c->Xref.p, c->Rd.p, c->skin, Gb, c->band_cells.start.p, c->band_cells.order.p,
                 c->band_coord.p, c->band_cand.p, c->band_slack.p, nband, &c->st.p->status, c->band.p, nx, ny, nz};
     launch_band_cand(BC, s);
     CK(cudaGetLastError());

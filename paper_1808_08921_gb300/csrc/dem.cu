@@ -788,25 +788,16 @@ __global__ void k_band_cand(BandCand B) {
                     bool dup = false;
                     for (int q = 0; q < nfound; ++q) dup |= c4[q] == p;
                     if (dup) continue;
-                    // offset in FP64 (centres up to the box length), wrapped
-                    // to the nearest image only when more than half a box
-                    // away, then FP32 (FP64 arithmetic is slow on this
-                    // part); the tests keep a superset of the candidates and
-                    // the slack is rounded down by a margin far above FP32
-                    // rounding, so a node is never re-tested too late
-                    float d2 = 0.f;
+                    double d2 = 0;
                     for (int q = 0; q < 3; ++q) {
                         double d = P[q] - B.X[3 * p + q];
-                        if (per[q] && (d > 0.5 * L[q] || d < -0.5 * L[q])) d -= L[q] * floor(d * iL[q] + 0.5);
-                        const float df = (float)d;
-                        d2 += df * df;
+                        if (per[q]) d -= L[q] * floor(d * iL[q] + 0.5);
+                        d2 += d * d;
                     }
-                    const float Rf = (float)B.R[p];
-                    const float r = Rf + (float)B.skin;
-                    if (d2 >= r * r * (1.0f + 1e-5f)) continue;
-                    const float dist = sqrtf(d2);
-                    slack = fmin(slack, (double)fmaxf(fabsf(dist - Rf) - 1e-5f * (1.0f + Rf), 0.0f));
-                    ninside += d2 < Rf * Rf * (1.0f + 1e-5f);
+                    double r = B.R[p] + B.skin;
+                    if (d2 >= r * r) continue;
+                    slack = fmin(slack, fabs(sqrt(d2) - B.R[p]));
+                    ninside += d2 < B.R[p] * B.R[p];
                     if (nfound >= 4) {
                         atomicOr(B.status, ST_CAPACITY);
                         continue;
