@@ -211,10 +211,12 @@ __global__ void __launch_bounds__(256, 4) k_links(Lat L, PartView P, LinkLists B
 void launch_links(const Lat& L, const PartView& P, const LinkLists& B, cudaStream_t s) {
     if (B.nwarps == 0) return;
     uint64_t threads = (uint64_t)B.nwarps * 32;  // one warp per LINK_WARP links
-    unsigned blocks = (unsigned)((threads + 255) / 256);
-    if (L.st == 0) launch_pdl(k_links<0>, blocks, 256, s, L, P, B);
-    else if (L.st == 1) launch_pdl(k_links<1>, blocks, 256, s, L, P, B);
-    else launch_pdl(k_links<2>, blocks, 256, s, L, P, B);
+    // two-warp blocks: the warps' run times vary with their links' scatter,
+    // and small blocks let the SMs refill as each pair finishes
+    unsigned blocks = (unsigned)((threads + 63) / 64);
+    if (L.st == 0) launch_pdl(k_links<0>, blocks, 64, s, L, P, B);
+    else if (L.st == 1) launch_pdl(k_links<1>, blocks, 64, s, L, P, B);
+    else launch_pdl(k_links<2>, blocks, 64, s, L, P, B);
 }
 
 // ------------------------------------------------------------ map update
@@ -617,10 +619,13 @@ void launch_map_update(const Lat& L, const PartView& P, const Band& band, const 
     MapArgs A{L, P, band, F, st, step_parity, after_even ? 1 : 0, lw};
     uint32_t nb = band.n > (uint32_t)P.n ? band.n : (uint32_t)P.n;
     if (nb == 0) nb = 1;
-    k_map_band<<<(nb + 255) / 256, 256, 0, s>>>(A);
+    // 64-thread blocks: most band nodes leave at the slack test, and small
+    // blocks keep the SMs busy with the few that go on to the sphere tests
+    k_map_band<<<(nb + 63) / 64, 64, 0, s>>>(A);
     if (band.n == 0) return;
-    // the queued count is read on the device: fixed grids stride over it
-    const unsigned grid = 2 * 152;
+    // the queued count is read on the device: fixed grids stride over it,
+    // sized for the few hundred conversions a step of a settling packing has
+    const unsigned grid = 4 * 152;
     if (L.st == 0) launch_pdl(k_map_gather_convert<0>, grid, MAP_THREADS, s, A);
     else if (L.st == 1) launch_pdl(k_map_gather_convert<1>, grid, MAP_THREADS, s, A);
     else launch_pdl(k_map_gather_convert<2>, grid, MAP_THREADS, s, A);
