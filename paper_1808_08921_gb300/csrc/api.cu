@@ -108,6 +108,7 @@ struct lbmdem_ctx {
     uint32_t nlink_raw = 0;  // link records before padding
     DBuf<uint2> linkw;       // link word of every stored node (even steps' links in the collide kernel)
     bool fused_links = false;
+    bool batched = false;  // steps being captured into a batch graph (columns share the GPU)
     DBuf<Flip> flip_rec;
     DBuf<float> flip_scratch;
     DBuf<uint8_t> flip_valid;
@@ -621,7 +622,8 @@ static void enqueue_step(lbmdem_ctx* c, int parity, bool monitor) {
         Band B{c->band_coord.p, c->band_cand.p, c->band_slack.p, c->nband};
         FlipBuf F{c->flip_rec.p, c->flip_scratch.p, c->flip_valid.p, c->flip_cap};
         if (tm) record_pair_begin(c, 2, e);
-        launch_map_update(L, P, B, F, c->st.p, parity == 1, parity, c->fused_links ? c->linkw.p : nullptr, s);
+        launch_map_update(L, P, B, F, c->st.p, parity == 1, parity, c->fused_links ? c->linkw.p : nullptr, c->batched,
+                          s);
         if (tm) record_pair_end(c, e);
         Mon mon{};
         DevStats* sd = c->st.p;
@@ -1226,7 +1228,9 @@ int capture_body(lbmdem_batch* b, lbmdem_ctx* c, cudaGraph_t body, int nsteps, v
                  const BatchCtl& ctl, int i, cudaGraphConditionalHandle h) {
     BCK(cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     const bool mon = c->p.monitor_every > 0;
+    c->batched = true;
     for (int k = 0; k < nsteps; ++k) enqueue_step(c, k & 1, mon && k == nsteps - 1);
+    c->batched = false;
     if (ctl_kernel) ctl_kernel<<<1, 32, 0, c->stream>>>(ctl, i, &c->st.p->status, h);
     cudaGraph_t g = body;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);

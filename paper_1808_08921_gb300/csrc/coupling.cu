@@ -614,18 +614,23 @@ __global__ void __launch_bounds__(SCATTER_THREADS) k_map_scatter(MapArgs A) {
     }
 }
 
+// Launch shapes: a column alone on the GPU takes small band blocks (most band
+// nodes leave at the slack test, and small blocks keep the SMs busy with the
+// few that go on to the sphere tests) and conversion grids of 4 x 152 blocks
+// (a settling packing converts a few hundred nodes per step); columns of a
+// batch, which share the GPU with each other, take 256-thread band blocks
+// and 152 conversion blocks, fewer blocks to schedule beside the other
+// columns' kernels.
 void launch_map_update(const Lat& L, const PartView& P, const Band& band, const FlipBuf& F,
-                       DevStats* st, bool after_even, int step_parity, uint2* lw, cudaStream_t s) {
+                       DevStats* st, bool after_even, int step_parity, uint2* lw, bool shared_gpu, cudaStream_t s) {
     MapArgs A{L, P, band, F, st, step_parity, after_even ? 1 : 0, lw};
     uint32_t nb = band.n > (uint32_t)P.n ? band.n : (uint32_t)P.n;
     if (nb == 0) nb = 1;
-    // 64-thread blocks: most band nodes leave at the slack test, and small
-    // blocks keep the SMs busy with the few that go on to the sphere tests
-    k_map_band<<<(nb + 63) / 64, 64, 0, s>>>(A);
+    const unsigned bb = shared_gpu ? 256 : 64;
+    k_map_band<<<(nb + bb - 1) / bb, bb, 0, s>>>(A);
     if (band.n == 0) return;
-    // the queued count is read on the device: fixed grids stride over it,
-    // sized for the few hundred conversions a step of a settling packing has
-    const unsigned grid = 4 * 152;
+    // the queued count is read on the device: fixed grids stride over it
+    const unsigned grid = shared_gpu ? 152 : 4 * 152;
     if (L.st == 0) launch_pdl(k_map_gather_convert<0>, grid, MAP_THREADS, s, A);
     else if (L.st == 1) launch_pdl(k_map_gather_convert<1>, grid, MAP_THREADS, s, A);
     else launch_pdl(k_map_gather_convert<2>, grid, MAP_THREADS, s, A);

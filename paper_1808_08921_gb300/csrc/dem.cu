@@ -393,7 +393,9 @@ __global__ void __launch_bounds__(DSM_THREADS, 1) k_dem_step_dsm(Dem D) {
         fixed = D.fixed[i] != 0;
         cnt = D.nb_cnt[i];
     }
-    // this lane's neighbour entries tl + u TEAM, u < NBT
+    // this lane's neighbour entries tl + u TEAM, u < NBT; the neighbour's CTA
+    // rank and slot are packed as (rank << 16) | slot once, so the substeps
+    // need no division by the spheres per CTA
     int nj[NBT];
     float4 ndr[NBT];
     float3 nh[NBT];
@@ -403,7 +405,8 @@ __global__ void __launch_bounds__(DSM_THREADS, 1) k_dem_step_dsm(Dem D) {
         nj[u] = -1;
         if (k < cnt) {
             size_t e = (size_t)i * D.nbmax + k;
-            nj[u] = D.nb_j[e];
+            const int j = D.nb_j[e], rk = j / spc;
+            nj[u] = (rk << 16) | (j - rk * spc);
             ndr[u] = D.nb_dref[e];
             nh[u] = f3(D.nb_ft[e]);
         }
@@ -447,12 +450,12 @@ __global__ void __launch_bounds__(DSM_THREADS, 1) k_dem_step_dsm(Dem D) {
 #pragma unroll
             for (int u = 0; u < NBT; ++u) {
                 if (nj[u] < 0) continue;
-                int rk = nj[u] / spc, lj = nj[u] - rk * spc;
+                const int rk = nj[u] >> 16, lj = nj[u] & 0xffff;
                 const float4* rx = cl.map_shared_rank(xchg, rk);
                 float4 xj = rx[(b * 3 + 0) * spc + lj], vj = rx[(b * 3 + 1) * spc + lj],
                        wj = rx[(b * 3 + 2) * spc + lj];
                 float4 h = make_float4(nh[u].x, nh[u].y, nh[u].z, 0.f);
-                pair_contact(D, Ri, __ldg(&D.R[nj[u]]), make_float3(xj.x - dx.x, xj.y - dx.y, xj.z - dx.z), ndr[u],
+                pair_contact(D, Ri, __ldg(&D.R[rk * spc + lj]), make_float3(xj.x - dx.x, xj.y - dx.y, xj.z - dx.z), ndr[u],
                              vh, wh, f3(vj), f3(wj), D.dt, h, F, T);
                 nh[u] = f3(h);
             }

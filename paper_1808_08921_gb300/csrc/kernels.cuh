@@ -194,7 +194,8 @@ void launch_read_fields(const Lat& L, bool after_even, double* rho, double* u, u
 // coupling.cu
 void launch_links(const Lat& L, const PartView& P, const LinkLists& B, cudaStream_t s);
 void launch_map_update(const Lat& L, const PartView& P, const Band& band, const FlipBuf& F,
-                       DevStats* st, bool after_even, int step_parity, uint2* lw, cudaStream_t s);
+                       DevStats* st, bool after_even, int step_parity, uint2* lw, bool shared_gpu,
+                       cudaStream_t s);
 void launch_link_words(const Lat& L, uint2* lw, cudaStream_t s);
 
 // dem.cu
