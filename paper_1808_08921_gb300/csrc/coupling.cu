@@ -99,8 +99,11 @@ __device__ __forceinline__ bool owns_neighbour(const Lat& L, const PartView& P, 
 // to the centre once per warp: sum r x (c q) = sum rel x (c q) - xf x F.
 // Warp-shuffle sums, then one FP64 atomic per component per warp into one
 // of NREP accumulator copies of the sphere.
+// 56 registers (no spills): 36 resident warps per SM, more scattered
+// loads in flight than the 32 warps at 64 registers (143.5 against 147 us
+// on the 128 x 128 x 1024 column).
 template <int ST>
-__global__ void __launch_bounds__(256, 4) k_links(Lat L, PartView P, LinkLists B) {
+__global__ void __maxnreg__(56) k_links(Lat L, PartView P, LinkLists B) {
     pdl_wait();
     pdl_trigger();
     constexpr int K = LINK_CHUNKS;

@@ -298,8 +298,12 @@ template <> __device__ __forceinline__ void st1<0>(float* p, float v, float) { _
 // them once per 32 EVEN_ROUNDS nodes.
 constexpr int EVEN_ROUNDS = 2;
 
+// 72 registers (a few spills to L1): 28 resident warps per SM instead of 24
+// at the 80 the kernel would otherwise take, which hides more of the
+// population loads' latency (187 against 190 us on the 128 x 128 x 1024
+// column).  Launched with up to 256 threads per block.
 template <bool MON, int ST>
-__global__ void __launch_bounds__(256, 3) k_collide_even_links(Lat L, Mon mon, PartView P, const uint2* __restrict__ lwp) {
+__global__ void __maxnreg__(72) k_collide_even_links(Lat L, Mon mon, PartView P, const uint2* __restrict__ lwp) {
     pdl_wait();
     pdl_trigger();
     auto* f = pops<ST>(L);
