@@ -103,9 +103,11 @@ typedef struct {
     int32_t link_mode;    /* 2: an even step's links (Eqs. 14-15, 18-19) are taken inside
                              its collide+stream kernel, an odd step's by the link kernel;
                              1: the link kernel every step; 0 (default): 2 with FP32
-                             storage, 1 with 16-bit storage.  Boxes narrower than
-                             2 (R + skin + 2) on a periodic axis always take 1.  Same
-                             results up to FP32 summation order.                       */
+                             storage and a largest sphere radius of 8 lattice units
+                             or more, else 1.  Boxes narrower than 2 (R + skin + 2)
+                             on a periodic axis, and packings of more than 16383
+                             spheres, always take 1.  Same results up to FP32
+                             summation order.                                          */
     void* cuda_stream;    /* cudaStream_t to issue on; NULL = a stream of the context */
 } lbmdem_params;
 

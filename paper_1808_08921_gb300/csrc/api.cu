@@ -525,10 +525,13 @@ static int build_layout(lbmdem_ctx* c, bool fresh) {
     // its links would need one lever per image, which the link lists keep
     const double reach = 2.0 * (c->Rmax + c->skin + 2.0);
     const bool wide = c->p.ny > reach && c->p.nz > reach && (!px || c->p.nx > reach);
-    // (link_mode 0: with FP32 storage only; with 16-bit storage the even
-    // collide kernel is bandwidth-light and the separate kernels measured
-    // faster)
-    const bool want = c->p.link_mode == 2 || (c->p.link_mode == 0 && c->p.storage == LBMDEM_F32);
+    // (link_mode 0: with FP32 storage and spheres of radius 8 lu or more.
+    // With 16-bit storage the even collide kernel is bandwidth-light, and
+    // smaller spheres change along a 32-node run often enough that the
+    // per-warp sphere sums cost more than the link kernel: R 5.7 FCC, 0.106
+    // against 0.091 ms per step; R 11.4, 0.309 against 0.329 ms)
+    const bool want = c->p.link_mode == 2 ||
+                      (c->p.link_mode == 0 && c->p.storage == LBMDEM_F32 && c->Rmax >= 8.0);
     c->fused_links = want && c->nwarps > 0 && np <= LW_MAX_SPHERES && wide;
     if (c->fused_links) {
         CK(c->linkw.ensure(nSpad));

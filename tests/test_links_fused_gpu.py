@@ -1,5 +1,6 @@
-"""An even step's links taken inside its collide+stream kernel (link_mode 0,
-the default: link words per node, sphere sums per warp) against the link
+"""An even step's links taken inside its collide+stream kernel (link_mode 2,
+the default for FP32 storage and spheres of radius 8 lu or more: link words
+per node, sphere sums per warp) against the link
 kernel every step (link_mode 1), and both against the FP64 oracle, including
 a fluid node whose solid neighbours belong to three spheres (the link word's
 owner-map fallback).
@@ -57,7 +58,7 @@ def test_links_in_collide_match_the_link_kernel(steps):
     """Moving spheres with conversions, after an even last step (1, 41) and an
     odd one (2)."""
     w = workloads.random_small(5, nx=40, ny=20, nz=20, n=8, R=3.5, vel=0.02, steps=steps)
-    _close(_run(w, steps, 0), _run(w, steps, 1), 3.5)
+    _close(_run(w, steps, 2), _run(w, steps, 1), 3.5)
 
 
 def _three_spheres():
@@ -93,11 +94,11 @@ def test_three_sphere_node_exists():
 @pytest.mark.parametrize("steps", [1, 30])
 def test_three_sphere_links_match_oracle_and_link_kernel(steps):
     w = _three_spheres()
-    a, b = _run(w, steps, 0), _run(w, steps, 1)
+    a, b = _run(w, steps, 2), _run(w, steps, 1)
     _close(a, b, 3.0)
     o = oracle.Oracle(w)
     o.step(steps)
-    g = lbmdem.Sim.from_workload(w)
+    g = lbmdem.Sim.from_workload(w, link_mode=2)
     try:
         g.step(steps)
         compare_fields(g, o)
@@ -118,15 +119,20 @@ def _launches(w, steps, mode, **over):
 def test_narrow_periodic_box_keeps_the_link_lists():
     """Where a node can neighbour two periodic images of one sphere (the
     12 x 12 cross-section of the saturated chains, R = 5.005) every step uses
-    the link lists, whose records carry the lever of their own image; a wide
-    box takes the even steps' links in the collide kernel (one launch fewer
-    per even step)."""
+    the link lists, whose records carry the lever of their own image, even
+    when the collide kernel's links are asked for; a wide box takes the even
+    steps' links in the collide kernel with link_mode 2 (one launch fewer per
+    even step), and by default only with spheres of radius 8 lu or more."""
     narrow = workloads.saturated_chain(True, steps=4)
-    assert _launches(narrow, 4, 0) == _launches(narrow, 4, 1)
+    assert _launches(narrow, 4, 0) == _launches(narrow, 4, 1) == _launches(narrow, 4, 2)
     wide = workloads.random_small(5, nx=40, ny=20, nz=20, n=8, R=3.5, vel=0.02, steps=4)
-    assert _launches(wide, 4, 1) - _launches(wide, 4, 0) == 2
+    assert _launches(wide, 4, 1) - _launches(wide, 4, 2) == 2
+    assert _launches(wide, 4, 0) == _launches(wide, 4, 1)
+    large = workloads.random_small(6, nx=48, ny=28, nz=28, n=2, R=8.5, vel=0.02, steps=4)
+    assert _launches(large, 4, 1) - _launches(large, 4, 0) == 2
     # the default takes the link kernel with 16-bit storage; mode 2 forces the
     # collide kernel's links there too
+    assert _launches(large, 4, 0, storage=lbmdem.F16_DEV) == _launches(large, 4, 1, storage=lbmdem.F16_DEV)
     f16 = dict(storage=lbmdem.F16_DEV)
     assert _launches(wide, 4, 0, **f16) == _launches(wide, 4, 1, **f16)
     assert _launches(wide, 4, 1, **f16) - _launches(wide, 4, 2, **f16) == 2

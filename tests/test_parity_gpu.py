@@ -87,13 +87,15 @@ def test_static_spheres_each_outlet(outlet):
         compare_particles(g, o)
 
 
-@pytest.mark.parametrize("seed", [1, 4])
-def test_moving_spheres_with_conversions(seed):
-    """Periodic box, spheres moving ~1 lu: nodes are covered and uncovered."""
+@pytest.mark.parametrize("seed,link_mode", [(1, 0), (4, 0), (1, 2)])
+def test_moving_spheres_with_conversions(seed, link_mode):
+    """Periodic box, spheres moving ~1 lu: nodes are covered and uncovered;
+    the default link path and the even steps' links in the collide kernel
+    (link words renewed at each conversion)."""
     w = workloads.random_small(seed, nx=22, ny=14, nz=12, n=3, R=3.1, tau=0.8, mobile=True, vel=0.05)
     w.inlet = workloads.X_PERIODIC
     w.rho_p, w.dem_substeps = 3.0, 3
-    g, o = _sim(w, skin=0.6, dem_skin=1.2), oracle.Oracle(w)
+    g, o = _sim(w, skin=0.6, dem_skin=1.2, link_mode=link_mode), oracle.Oracle(w)
     o0 = o.owner().copy()
     for n in (2, 17, 41):
         g.step(n)
@@ -202,8 +204,8 @@ def test_fp64_monitors_match_oracle_totals(workload):
     step sums the state it starts from; with fixed spheres no node converts,
     so that is the oracle's state after the same number of completed steps.
     Graph-captured runs monitor their last (odd) step; five single steps
-    with monitor_every = 5 monitor step 4, an even step (whose collide
-    kernel takes the step's links)."""
+    with monitor_every = 5 monitor step 4, an even step, here with the
+    step's links inside its collide kernel (link_mode 2)."""
     steps, every = 48, 16
     if workload == "plane_wave":
         w = workloads.plane_wave(nx=200, ny=2, nz=3, amplitude=1e-3, omega=0.05, steps=48)
@@ -212,7 +214,8 @@ def test_fp64_monitors_match_oracle_totals(workload):
         w.fixed = np.ones(len(w.R), np.uint8)
         if workload == "column_even_step":
             steps, every = 5, 5
-    g, o = _sim(w, monitor_every=every), oracle.Oracle(w)
+    over = dict(link_mode=2) if workload == "column_even_step" else {}
+    g, o = _sim(w, monitor_every=every, **over), oracle.Oracle(w)
     g.step(steps)
     mon = g.monitors()
     k = int(mon[5])

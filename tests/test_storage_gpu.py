@@ -59,11 +59,11 @@ class _Snap:
 
 
 @pytest.mark.parametrize("storage,link_mode", [(lbmdem.F32, 0), (lbmdem.F16_DEV, 0), (lbmdem.BF16_DEV, 0),
-                                               (lbmdem.F16_DEV, 2), (lbmdem.BF16_DEV, 2)])
+                                               (lbmdem.F32, 2), (lbmdem.F16_DEV, 2), (lbmdem.BF16_DEV, 2)])
 def test_storage_error_against_oracle(reference, storage, link_mode):
-    """link_mode 0: the default path for the storage (the collide kernel's
-    links with FP32, the link kernel with 16 bits); 2: the collide kernel's
-    links on 16-bit populations."""
+    """link_mode 0: the default path (the link kernel every step here: the
+    column's spheres have R 5.7); 2: an even step's links inside its collide
+    kernel, on FP32 and on 16-bit populations."""
     w, snaps = reference
     g = lbmdem.Sim.from_workload(w, storage=storage, link_mode=link_mode)
     done = 0
