@@ -92,40 +92,136 @@ size_t scan_tmp_size(size_t n) {
     return t + 1;
 }
 
-// ------------------------------------------------------------ painting
+// ------------------------------------------------------------ box lines
 
 __device__ __forceinline__ int wrapi(int a, int L) {
     int r = a % L;
     return r < 0 ? r + L : r;
 }
 
+// The nodes of a sphere's box [x0, x0 + ex) x [y0, y0 + ey) x [z0, z1] that
+// a kernel has to visit: on each line (x, y) at most two z-intervals
+// [a0, a1] and [b0, b1] (empty when lo > hi), given by the caller from the
+// line's distance to the centre; the rest of the box is known to need
+// nothing.  One thread block per sphere (BOX_THREADS threads): lines are
+// taken BOX_THREADS at a time, a block scan places their nodes, and each
+// round gives every thread one node in (x, y, z) order -- the order of the
+// whole-box loop with the skipped nodes left out.  Every thread calls
+// `body(valid, x, y, z)` in every round (valid false past the last node), so
+// the body may synchronise the block.
+constexpr int BOX_THREADS = 256;
+
+struct LineSpan {
+    int a0, a1, b0, b1;
+};
+
+struct BoxLines {
+    int x0, y0, z0, z1, ex, ey;
+};
+
+// the nodes with |z - zc| <= a, minus those with |z - zc| < b (b <= 0: none
+// removed), within [z0, z1]
+__device__ __forceinline__ LineSpan line_span(double zc, double a2, double b2, int z0, int z1) {
+    LineSpan s = {0, -1, 0, -1};
+    if (!(a2 >= 0.0)) return s;
+    const double a = sqrt(a2);
+    const int lo = max(z0, (int)ceil(zc - a)), hi = min(z1, (int)floor(zc + a));
+    if (lo > hi) return s;
+    s.a0 = lo;
+    s.a1 = hi;
+    if (b2 > 0.0) {
+        const double b = sqrt(b2);
+        const int e0 = (int)floor(zc - b) + 1, e1 = (int)ceil(zc + b) - 1;  // strictly inside
+        if (e0 <= e1) {
+            s.a1 = min(hi, e0 - 1);
+            s.b0 = max(lo, e1 + 1);
+            s.b1 = hi;
+        }
+    }
+    return s;
+}
+
+template <class SpanFn, class Body>
+__device__ void for_box_nodes(const BoxLines& B, SpanFn span, Body body) {
+    __shared__ int s_a0[BOX_THREADS], s_la[BOX_THREADS], s_b0[BOX_THREADS];
+    __shared__ uint32_t s_start[BOX_THREADS + 1];
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t nlines = (uint32_t)B.ex * (uint32_t)B.ey;
+    for (uint32_t l0 = 0; l0 < nlines; l0 += nt) {
+        LineSpan sp = {0, -1, 0, -1};
+        if (l0 + tid < nlines) sp = span(B.x0 + (int)((l0 + tid) / (uint32_t)B.ey), B.y0 + (int)((l0 + tid) % (uint32_t)B.ey));
+        const int la = max(sp.a1 - sp.a0 + 1, 0), lb = max(sp.b1 - sp.b0 + 1, 0);
+        s_a0[tid] = sp.a0;
+        s_la[tid] = la;
+        s_b0[tid] = sp.b0;
+        s_start[tid + 1] = (uint32_t)(la + lb);
+        if (tid == 0) s_start[0] = 0u;
+        __syncthreads();
+        for (uint32_t o = 1; o < nt; o <<= 1) {  // inclusive scan of the counts
+            const uint32_t v = tid >= o ? s_start[tid + 1 - o] : 0u;
+            __syncthreads();
+            s_start[tid + 1] += v;
+            __syncthreads();
+        }
+        const uint32_t total = s_start[nt];
+        for (uint32_t c0 = 0; c0 < total; c0 += nt) {
+            const uint32_t c = c0 + tid;
+            const bool valid = c < total;
+            int xi = 0, yi = 0, zi = 0;
+            if (valid) {
+                uint32_t lo = 0, hi = nt;  // s_start[lo] <= c < s_start[hi]
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (s_start[mid] <= c) lo = mid;
+                    else hi = mid;
+                }
+                const int o = (int)(c - s_start[lo]);
+                zi = o < s_la[lo] ? s_a0[lo] + o : s_b0[lo] + (o - s_la[lo]);
+                xi = B.x0 + (int)((l0 + lo) / (uint32_t)B.ey);
+                yi = B.y0 + (int)((l0 + lo) % (uint32_t)B.ey);
+            }
+            body(valid, xi, yi, zi);
+        }
+        __syncthreads();  // the next batch rewrites the spans
+    }
+}
+
+// ------------------------------------------------------------ painting
+
+// Nodes farther than R + skin from the centre are left alone (neither
+// owned, deep nor band), so each line visits |z - Z| <= sqrt((R + skin +
+// 0.01)^2 - rho^2) only.
 template <int PASS>
-__global__ void k_paint(PaintArgs A) {
-    int p = blockIdx.x;
-    double X0 = A.X[3 * p], X1 = A.X[3 * p + 1], X2 = A.X[3 * p + 2];
-    double R = A.R[p];
-    double reach = R + A.skin + 1.0;
-    int x0 = (int)ceil(X0 - reach), x1 = (int)floor(X0 + reach);
-    int y0 = (int)ceil(X1 - reach), y1 = (int)floor(X1 + reach);
-    int z0 = (int)ceil(X2 - reach), z1 = (int)floor(X2 + reach);
-    int ex = x1 - x0 + 1, ey = y1 - y0 + 1, ez = z1 - z0 + 1;
-    long long vol = (long long)ex * ey * ez;
-    double Rin = R - A.skin, Rout = R + A.skin;
-    for (long long t = threadIdx.x; t < vol; t += blockDim.x) {
-        int zi = z0 + (int)(t % ez);
-        long long r = t / ez;
-        int yi = y0 + (int)(r % ey);
-        int xi = x0 + (int)(r / ey);
+__global__ void __launch_bounds__(BOX_THREADS) k_paint(PaintArgs A) {
+    const int p = blockIdx.x;
+    const double X0 = A.X[3 * p], X1 = A.X[3 * p + 1], X2 = A.X[3 * p + 2];
+    const double R = A.R[p];
+    const double reach = R + A.skin + 1.0;
+    BoxLines B;
+    B.x0 = (int)ceil(X0 - reach);
+    B.y0 = (int)ceil(X1 - reach);
+    B.z0 = (int)ceil(X2 - reach);
+    B.z1 = (int)floor(X2 + reach);
+    B.ex = (int)floor(X0 + reach) - B.x0 + 1;
+    B.ey = (int)floor(X1 + reach) - B.y0 + 1;
+    const double Rin = R - A.skin, Rout = R + A.skin;
+    const double rv = Rout + 0.01;
+    auto span = [&](int xi, int yi) {
+        const double ax = (double)xi - X0, ay = (double)yi - X1;
+        return line_span(X2, rv * rv - (ax * ax + ay * ay), 0.0, B.z0, B.z1);
+    };
+    for_box_nodes(B, span, [&](bool valid, int xi, int yi, int zi) {
+        if (!valid) return;
         int x;
         if (A.px) {
             x = wrapi(xi, A.nx);
         } else {
-            if (xi <= 0 || xi >= A.nx - 1) continue;  // boundary planes stay fluid
+            if (xi <= 0 || xi >= A.nx - 1) return;  // boundary planes stay fluid
             x = xi;
         }
-        int y = wrapi(yi, A.ny), z = wrapi(zi, A.nz);
-        double ax = (double)xi - X0, ay = (double)yi - X1, az = (double)zi - X2;
-        size_t li = ((size_t)x * A.ny + y) * A.nz + z;
+        const int y = wrapi(yi, A.ny), z = wrapi(zi, A.nz);
+        const double ax = (double)xi - X0, ay = (double)yi - X1, az = (double)zi - X2;
+        const size_t li = ((size_t)x * A.ny + y) * A.nz + z;
         if (A.owner && inside_exact(ax, ay, az, R)) {
             unsigned long long rb = (unsigned long long)__double_as_longlong(inside_ratio(ax, ay, az, R));
             if (PASS == 0)
@@ -133,11 +229,11 @@ __global__ void k_paint(PaintArgs A) {
             else if (A.best[li] == rb)
                 atomicMin(&A.owner[li], p);
         }
-        if (PASS == 1) continue;
-        double d2 = ax * ax + ay * ay + az * az;
+        if (PASS == 1) return;
+        const double d2 = ax * ax + ay * ay + az * az;
         if (Rin > 0 && d2 < Rin * Rin) A.deep[li] = 1;
         if (d2 < Rout * Rout && (Rin <= 0 || d2 >= Rin * Rin)) A.band[li] = 1;
-    }
+    });
 }
 
 // word masks: maskF = maskA = stored fluid, maskB = stored solid
@@ -251,13 +347,7 @@ struct SurfNode {
 // link nodes, and the image test separates distances below R (owned) from
 // distances above L - R - skin (another image), both at least the skin away
 // from R + skin.
-__device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, uint32_t t, int x0, int y0, int z0,
-                                          int ey, int ez, SurfNode& sn) {
-    const uint32_t r = t / (uint32_t)ez;
-    int zi = z0 + (int)(t - r * (uint32_t)ez);
-    const uint32_t q = r / (uint32_t)ey;
-    int yi = y0 + (int)(r - q * (uint32_t)ey);
-    int xi = x0 + (int)q;
+__device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, int xi, int yi, int zi, SurfNode& sn) {
     int x;
     if (A.L.px) x = wrapi(xi, A.L.nx);
     else {
@@ -311,27 +401,51 @@ __device__ __forceinline__ bool surf_node(const SurfArgs& A, int p, uint32_t t, 
     return true;
 }
 
+// The candidates of sphere p's surface lists: the box of the reach test,
+// line by line from the inner radius R - skin - 0.01 (deeper nodes are
+// never stored, except on the non-periodic boundary planes, which are
+// never deep) to the reach test's radius with a relative margin of 1e-4
+// over its FP32 rounding.  surf_node() still decides every candidate, so the
+// lists are those of the whole box, in the same order.
+__device__ __forceinline__ BoxLines surf_box(const SurfArgs& A, int p) {
+    const double reach = A.R[p] + A.reach_extra;
+    BoxLines B;
+    B.x0 = (int)ceil(A.X[3 * p] - reach);
+    B.y0 = (int)ceil(A.X[3 * p + 1] - reach);
+    B.z0 = (int)ceil(A.X[3 * p + 2] - reach);
+    B.z1 = (int)floor(A.X[3 * p + 2] + reach);
+    B.ex = (int)floor(A.X[3 * p] + reach) - B.x0 + 1;
+    B.ey = (int)floor(A.X[3 * p + 1] + reach) - B.y0 + 1;
+    return B;
+}
+
+__device__ __forceinline__ LineSpan surf_span(const SurfArgs& A, int p, int xi, int yi, int z0, int z1) {
+    const double X0 = A.X[3 * p], X1 = A.X[3 * p + 1], X2 = A.X[3 * p + 2];
+    const double reach = (double)((float)A.R[p] + (float)A.reach_extra);
+    const double ax = (double)xi - X0, ay = (double)yi - X1, rho2 = ax * ax + ay * ay;
+    const double rin = A.R[p] - A.skin - 0.01;
+    const bool plane = !A.L.px && (xi == 0 || xi == A.L.nx - 1);
+    const double b2 = rin > 0.0 && !plane ? rin * rin - rho2 : 0.0;
+    return line_span(X2, reach * reach * (1.0 + 1e-4) + 0.05 - rho2, b2, z0, z1);
+}
+
 // per sphere: links per direction, padded to whole 32-record chunks; the
 // sphere's total is padded to whole LINK_WARP groups on its last direction
-__global__ void k_surf_count(SurfArgs A) {
-    int p = blockIdx.x;
-    double reach = A.R[p] + A.reach_extra;
-    int x0 = (int)ceil(A.X[3 * p] - reach), x1 = (int)floor(A.X[3 * p] + reach);
-    int y0 = (int)ceil(A.X[3 * p + 1] - reach), y1 = (int)floor(A.X[3 * p + 1] + reach);
-    int z0 = (int)ceil(A.X[3 * p + 2] - reach), z1 = (int)floor(A.X[3 * p + 2] + reach);
-    int ey = y1 - y0 + 1, ez = z1 - z0 + 1;
-    const uint32_t vol = (uint32_t)(x1 - x0 + 1) * (uint32_t)ey * (uint32_t)ez;
+__global__ void __launch_bounds__(BOX_THREADS) k_surf_count(SurfArgs A) {
+    const int p = blockIdx.x;
+    const BoxLines B = surf_box(A, p);
     __shared__ uint32_t cnt[LINK_GROUPS];
     if (threadIdx.x < LINK_GROUPS) cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < vol; t += blockDim.x) {
-        SurfNode sn;
-        if (!surf_node(A, p, t, x0, y0, z0, ey, ez, sn)) continue;
-        for (int m = 0; m < Q - 1; ++m) {
-            if (sn.sure >> m & 1u) atomicAdd(&cnt[2 * m], 1u);
-            if (sn.maybe >> m & 1u) atomicAdd(&cnt[2 * m + 1], 1u);
-        }
-    }
+    for_box_nodes(B, [&](int xi, int yi) { return surf_span(A, p, xi, yi, B.z0, B.z1); },
+                  [&](bool valid, int xi, int yi, int zi) {
+                      SurfNode sn;
+                      if (!valid || !surf_node(A, p, xi, yi, zi, sn)) return;
+                      for (int m = 0; m < Q - 1; ++m) {
+                          if (sn.sure >> m & 1u) atomicAdd(&cnt[2 * m], 1u);
+                          if (sn.maybe >> m & 1u) atomicAdd(&cnt[2 * m + 1], 1u);
+                      }
+                  });
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t tot = 0, raw = 0;
@@ -347,25 +461,20 @@ __global__ void k_surf_count(SurfArgs A) {
     if (threadIdx.x < LINK_GROUPS) A.count[(size_t)p * LINK_GROUPS + threadIdx.x] = cnt[threadIdx.x];
 }
 
-// fill in a deterministic order: per direction, chunks of blockDim nodes in
-// bounding-box order, block prefix sums over the chunk
-__global__ void k_surf_fill(SurfArgs A) {
-    int p = blockIdx.x;
-    double reach = A.R[p] + A.reach_extra;
-    int x0 = (int)ceil(A.X[3 * p] - reach), x1 = (int)floor(A.X[3 * p] + reach);
-    int y0 = (int)ceil(A.X[3 * p + 1] - reach), y1 = (int)floor(A.X[3 * p + 1] + reach);
-    int z0 = (int)ceil(A.X[3 * p + 2] - reach), z1 = (int)floor(A.X[3 * p + 2] + reach);
-    int ey = y1 - y0 + 1, ez = z1 - z0 + 1;
-    const uint32_t vol = (uint32_t)(x1 - x0 + 1) * (uint32_t)ey * (uint32_t)ez;
+// fill in a deterministic order: per direction, rounds of blockDim
+// candidates in bounding-box order, block prefix sums over the round
+__global__ void __launch_bounds__(BOX_THREADS) k_surf_fill(SurfArgs A) {
+    const int p = blockIdx.x;
+    const BoxLines B = surf_box(A, p);
     __shared__ uint32_t sh[LINK_GROUPS][33];
     __shared__ uint32_t run[LINK_GROUPS];
     if (threadIdx.x < LINK_GROUPS) run[threadIdx.x] = 0;
     __syncthreads();
     uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (uint32_t t0 = 0; t0 < vol; t0 += blockDim.x) {
-        const uint32_t t = t0 + threadIdx.x;
+    for_box_nodes(B, [&](int xi, int yi) { return surf_span(A, p, xi, yi, B.z0, B.z1); },
+                  [&](bool valid, int xi, int yi, int zi) {
         SurfNode sn;
-        bool ok = t < vol && surf_node(A, p, t, x0, y0, z0, ey, ez, sn);
+        bool ok = valid && surf_node(A, p, xi, yi, zi, sn);
         // group 2 m + 1 takes the `maybe` links of direction m, 2 m the others
         uint32_t sure = ok ? sn.sure : 0u, maybe = ok ? sn.maybe : 0u;
         for (int g = 0; g < LINK_GROUPS; ++g) {
@@ -399,7 +508,7 @@ __global__ void k_surf_fill(SurfArgs A) {
         __syncthreads();
         if (threadIdx.x < LINK_GROUPS) run[threadIdx.x] += sh[threadIdx.x][32];
         __syncthreads();
-    }
+    });
     // pad every group to its chunks
     for (int g = 0; g < LINK_GROUPS; ++g) {
         size_t gi = (size_t)p * LINK_GROUPS + g;
