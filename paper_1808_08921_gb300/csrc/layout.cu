@@ -2,8 +2,9 @@
 //
 // Run at set_packing and at every re-layout (when some sphere has moved a
 // good part of the skin since the last one).  Steps:
-//   1. paint: for every sphere, every node of its bounding box (all periodic
-//      images) is tested with the exact FP64 rule |y - X|^2 < R^2 shared with
+//   1. paint: for every sphere, every node within R + skin of its centre
+//      (all periodic images; the box's lines visit only that ball) is
+//      tested with the exact FP64 rule |y - X|^2 < R^2 shared with
 //      the map update; a node inside several spheres belongs to the one with
 //      the smallest |y - X|^2 / R^2 (first pass: atomicMin of the FP64 ratio
 //      bits; second pass: lowest index among the equal ratios).
@@ -17,7 +18,8 @@
 //   2. word masks and counts per 32-node word; exclusive scans give the
 //      compact indices (region A = fluid now, region B = stored solid).
 //   3. compact coordinates, fluid bits, band list with candidate spheres,
-//      per-sphere surface lists for the link kernel (warp-padded), and, on a
+//      per-sphere surface lists for the link kernel (warp-padded; the box's
+//      lines visit only the shell where link nodes can be), and, on a
 //      re-layout, the populations copied from the old compact order.
 #include "common.cuh"
 #include "kernels.cuh"
@@ -541,8 +543,8 @@ __global__ void k_fill_u64(unsigned long long* p, unsigned long long v, size_t n
 void launch_paint(const PaintArgs& A, int n, size_t N, cudaStream_t s) {
     if (n <= 0) return;
     if (A.owner) k_fill_u64<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(A.best, ~0ull, N);
-    k_paint<0><<<n, 256, 0, s>>>(A);
-    if (A.owner) k_paint<1><<<n, 256, 0, s>>>(A);
+    k_paint<0><<<n, BOX_THREADS, 0, s>>>(A);
+    if (A.owner) k_paint<1><<<n, BOX_THREADS, 0, s>>>(A);
 }
 
 void launch_words(const LayoutArgs& A, cudaStream_t s) {
@@ -578,11 +580,11 @@ void launch_band_collect(const LayoutArgs& A, uint32_t* band_coord, uint32_t* co
 }
 
 void launch_surf_count(const SurfArgs& A, int n, cudaStream_t s) {
-    if (n > 0) k_surf_count<<<n, 256, 0, s>>>(A);
+    if (n > 0) k_surf_count<<<n, BOX_THREADS, 0, s>>>(A);
 }
 
 void launch_surf_fill(const SurfArgs& A, int n, cudaStream_t s) {
-    if (n > 0) k_surf_fill<<<n, 256, 0, s>>>(A);
+    if (n > 0) k_surf_fill<<<n, BOX_THREADS, 0, s>>>(A);
 }
 
 }  // namespace lbmdem
